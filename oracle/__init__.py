@@ -1,0 +1,158 @@
+"""FP64 CPU oracle for the SPARKLING hot path (arxiv 2108.02991).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It never imports the
+CUDA library and the CUDA library never imports it; the two share no code.
+
+The arithmetic lives in ``sparkling_oracle.c`` (plain C, IEEE double,
+``-ffp-contract=off``); this module only builds it with gcc and marshals
+NumPy arrays.  See the C file for the definitions followed:
+
+* ``forces``  -- A_i, R_i, G_i = A_i - R_i (Sec. II-C, eqs. attraction_term,
+  repulsion_term, attraction_derivative_basic, Fr_grad with H = |.|_2);
+* ``energy``  -- F^a, F^r (eqs. global_minimization, attraction_term,
+  repulsion_term);
+* ``project`` -- per-shot projection onto the constraint set (eq. constraints,
+  Sec. II-D, Suppl. Sec. I) by FISTA on the dual;
+* ``violation`` -- the constraint checker;
+* ``step``    -- one projected-gradient step (eq. proj_grad_descent).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sparkling_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOTCONV = 0, 1, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (OpenMP, -O2, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
+            lib.oracle_forces.argtypes = [p, i64, p, i64, i64, i64, d, d, p, i64, p, p, p, p, p]
+            lib.oracle_energy.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p]
+            lib.oracle_project.argtypes = [p, p, i64, i64, d, d, d, i64, p, i64, d, d, i64, p]
+            lib.oracle_violation.argtypes = [p, i64, i64, d, d, d, i64, p, p]
+            lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64]
+            for f in (lib.oracle_forces, lib.oracle_energy, lib.oracle_project,
+                      lib.oracle_violation, lib.oracle_step):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _grid_args(grid):
+    rho = _f64(grid.rho)
+    nx, ny, nz = (int(v) for v in grid.n)
+    if rho.size != nx * ny * nz:
+        raise ValueError("rho size does not match grid.n")
+    return rho, nx, ny, nz, float(grid.lo), float(grid.hi)
+
+
+def forces(K, grid, targets=None, energies: bool = False):
+    """Return (A, R, G) as float64 [M, 3] for the target indices (all if None);
+    with ``energies`` also the per-target sums (ea, er)."""
+    K = _f64(K)
+    N = K.shape[0]
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    if targets is None:
+        tptr, M = None, N
+    else:
+        targets = np.ascontiguousarray(np.asarray(targets, dtype=np.int64))
+        tptr, M = _ptr(targets), targets.size
+    A = np.empty((M, 3)); R = np.empty((M, 3)); G = np.empty((M, 3))
+    ea = np.empty(M); er = np.empty(M)
+    st = _load().oracle_forces(_ptr(K), N, _ptr(rho), nx, ny, nz, lo, hi, tptr, M,
+                               _ptr(A), _ptr(R), _ptr(G), _ptr(ea), _ptr(er))
+    if st != OK:
+        raise ValueError(f"oracle_forces failed ({st})")
+    return (A, R, G, ea, er) if energies else (A, R, G)
+
+
+def energy(K, grid):
+    """Return (F, F^a, F^r)."""
+    K = _f64(K)
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    fa, fr = ctypes.c_double(), ctypes.c_double()
+    st = _load().oracle_energy(_ptr(K), K.shape[0], _ptr(rho), nx, ny, nz, lo, hi,
+                               ctypes.byref(fa), ctypes.byref(fr))
+    if st != OK:
+        raise ValueError(f"oracle_energy failed ({st})")
+    return fa.value - fr.value, fa.value, fr.value
+
+
+def project(K, Nc, Ns, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0), n_iter=100,
+            tol=0.0, margin=0.0, check_every=10, return_iters=False):
+    """Project each of Nc shots of Ns samples; returns a new float64 [N, 3]
+    (and the per-shot iteration counts).  Raises on invalid input; in
+    converged mode (tol > 0) a shot that did not converge raises RuntimeError."""
+    K = _f64(K).reshape(-1, 3)
+    if K.shape[0] != Nc * Ns:
+        raise ValueError("K must hold Nc*Ns samples")
+    out = np.empty_like(K)
+    pin_a = _f64(pin)
+    iters = np.zeros(max(Nc, 1), dtype=np.int64)
+    st = _load().oracle_project(_ptr(K), _ptr(out), Nc, Ns, alpha, beta, box, pin_index,
+                                _ptr(pin_a), n_iter, tol, margin, check_every, _ptr(iters))
+    if st == ENOTCONV:
+        raise RuntimeError("oracle projection did not converge")
+    if st != OK:
+        raise ValueError(f"oracle_project failed ({st})")
+    return (out, iters[:Nc]) if return_iters else out
+
+
+def violation(K, Nc, Ns, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0)):
+    """Largest (amplitude, slew, box, pin) violation over all shots."""
+    K = _f64(K).reshape(-1, 3)
+    out = np.zeros(4)
+    pin_a = _f64(pin)
+    st = _load().oracle_violation(_ptr(K), Nc, Ns, alpha, beta, box, pin_index, _ptr(pin_a),
+                                  _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_violation failed ({st})")
+    return out
+
+
+def step(K, Nc, Ns, grid, eta, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0),
+         n_iter=100):
+    """One projected-gradient step K <- Pi(K - eta G); returns a new array."""
+    K = _f64(K).reshape(-1, 3).copy()
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    pin_a = _f64(pin)
+    st = _load().oracle_step(_ptr(K), Nc, Ns, _ptr(rho), nx, ny, nz, lo, hi, eta, alpha, beta,
+                             box, pin_index, _ptr(pin_a), n_iter)
+    if st != OK:
+        raise ValueError(f"oracle_step failed ({st})")
+    return K

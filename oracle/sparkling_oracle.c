@@ -1,0 +1,399 @@
+/*
+ * FP64 CPU oracle for the SPARKLING hot path (arxiv 2108.02991).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header
+ * or constant with the CUDA library and never calls it.
+ *
+ * Everything is computed in IEEE double, built with -ffp-contract=off so the
+ * arithmetic is the same sequence of roundings on every host.  Sums run in
+ * index order; OpenMP only splits independent targets (or shots), so results
+ * do not depend on the thread count.
+ *
+ * Notation (Sec. II-B, eqs. attraction_term / repulsion_term with H = |.|_2):
+ *   K[i] in [-1/2,1/2]^3, i = 0..N-1 (shot after shot);
+ *   density points x_q at the cell centres of an nx x ny x nz grid over
+ *   [lo,hi]^3, weights rho_q (array [nz][ny][nx], x fastest);
+ *   A_i = sum_q rho_q (K_i - x_q) / |K_i - x_q|          (attraction force)
+ *   R_i = (1/N) sum_{j != i} (K_i - K_j) / |K_i - K_j|   (repulsion force)
+ *   G_i = A_i - R_i = N dF/dK_i                          (eq. Fr_grad, H' = 1)
+ *   F^a = (1/N) sum_i sum_q rho_q |K_i - x_q|
+ *   F^r = (1/(2N^2)) sum_{i != j} |K_i - K_j|
+ * A term whose difference vector is exactly zero contributes nothing (the
+ * minimum-norm subgradient of |.| at 0; the paper only excludes j = i).
+ *
+ * Projection (Sec. II-D and Suppl. Sec. I): each shot s in R^{Ns x 3} is
+ * projected onto {|s|_inf <= box, s[pin] = v, |D1 s|_{2,inf} <= alpha,
+ * |D2 s|_{2,inf} <= beta} (eq. constraints) by accelerated proximal gradient
+ * (FISTA) on the Fenchel dual of min 1/2 |s - k|^2.  The paper delegates the
+ * algorithm to its reference [Chauffert TMI'16]; the dual form used here is:
+ *   D1 s[n] = s[n+1] - s[n]            n = 0..Ns-2
+ *   D2 s[n] = s[n+2] - 2 s[n+1] + s[n] n = 0..Ns-3
+ *   primal map  s(q) = pin(clip_box(k - D1^T q1 - D2^T q2))
+ *   step tau = 1/20  (|D1|^2 <= 4, |D2|^2 <= 16)
+ *   z = y + tau D s(y);  q+ = z - P_{ball(tau*alpha)}(z) row-wise (and beta)
+ *   t+ = (1 + sqrt(1 + 4 t^2)) / 2;  y = q+ + ((t - 1) / t+) (q+ - q)
+ *   output s(q) after n_iter iterations (q = y = 0, t = 1 at the start).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL 1
+#define ORACLE_ENOTCONV 6
+
+/* Cell-centre coordinate of cell q of n over [lo, hi]. */
+static double centre(int64_t q, int64_t n, double lo, double hi)
+{
+    return lo + ((double)q + 0.5) * ((hi - lo) / (double)n);
+}
+
+/* Attraction force and energy sum of one target position (kx,ky,kz). */
+static void attraction_one(double kx, double ky, double kz, const double *rho,
+                           int64_t nx, int64_t ny, int64_t nz, double lo, double hi,
+                           double out[3], double *energy)
+{
+    double ax = 0.0, ay = 0.0, az = 0.0, e = 0.0;
+    for (int64_t iz = 0; iz < nz; ++iz) {
+        double z = centre(iz, nz, lo, hi);
+        for (int64_t iy = 0; iy < ny; ++iy) {
+            double y = centre(iy, ny, lo, hi);
+            const double *row = rho + (iz * ny + iy) * nx;
+            for (int64_t ix = 0; ix < nx; ++ix) {
+                double x = centre(ix, nx, lo, hi);
+                double dx = kx - x, dy = ky - y, dz = kz - z;
+                double r = sqrt(dx * dx + dy * dy + dz * dz);
+                if (r == 0.0)
+                    continue;
+                double w = row[ix];
+                ax += w * (dx / r);
+                ay += w * (dy / r);
+                az += w * (dz / r);
+                e += w * r;
+            }
+        }
+    }
+    out[0] = ax; out[1] = ay; out[2] = az;
+    *energy = e;
+}
+
+/* Sum over j != i of the unit vectors (K_i - K_j)/|K_i - K_j| and of the
+ * distances |K_i - K_j| (not yet scaled by 1/N). */
+static void repulsion_one(const double *K, int64_t N, int64_t i, double out[3], double *energy)
+{
+    double kx = K[3 * i], ky = K[3 * i + 1], kz = K[3 * i + 2];
+    double rx = 0.0, ry = 0.0, rz = 0.0, e = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (j == i)
+            continue;
+        double dx = kx - K[3 * j], dy = ky - K[3 * j + 1], dz = kz - K[3 * j + 2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0)
+            continue;
+        rx += dx / r;
+        ry += dy / r;
+        rz += dz / r;
+        e += r;
+    }
+    out[0] = rx; out[1] = ry; out[2] = rz;
+    *energy = e;
+}
+
+/*
+ * Forces for M targets.  targets[m] is an index into K (targets == NULL means
+ * m itself, with M = N).  Writes A, R and G = A - R as [M][3] (any of them may
+ * be NULL), and per-target energy sums ea[m] = sum_q rho_q |K_i - x_q|,
+ * er[m] = sum_{j != i} |K_i - K_j| (may be NULL).
+ */
+int oracle_forces(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,
+                  int64_t nz, double lo, double hi, const int64_t *targets, int64_t M,
+                  double *A, double *R, double *G, double *ea, double *er)
+{
+    if (!K || N < 1 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo) || M < 0)
+        return ORACLE_EINVAL;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t m = 0; m < M; ++m) {
+        int64_t i = targets ? targets[m] : m;
+        if (i < 0 || i >= N) {
+            bad = 1;
+            continue;
+        }
+        double a[3], r[3], eA, eR;
+        attraction_one(K[3 * i], K[3 * i + 1], K[3 * i + 2], rho, nx, ny, nz, lo, hi, a, &eA);
+        repulsion_one(K, N, i, r, &eR);
+        for (int c = 0; c < 3; ++c) {
+            double rc = r[c] / (double)N;
+            if (A) A[3 * m + c] = a[c];
+            if (R) R[3 * m + c] = rc;
+            if (G) G[3 * m + c] = a[c] - rc;
+        }
+        if (ea) ea[m] = eA;
+        if (er) er[m] = eR;
+    }
+    return bad ? ORACLE_EINVAL : ORACLE_OK;
+}
+
+/* Energy F = F^a - F^r (eqs. global_minimization, attraction_term,
+ * repulsion_term); the per-target sums are added in index order. */
+int oracle_energy(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,
+                  int64_t nz, double lo, double hi, double *Fa, double *Fr)
+{
+    double *ea = (double *)malloc(sizeof(double) * (size_t)N);
+    double *er = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!ea || !er) {
+        free(ea); free(er);
+        return ORACLE_EINVAL;
+    }
+    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, NULL, ea, er);
+    if (st == ORACLE_OK) {
+        double sa = 0.0, sr = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            sa += ea[i];
+            sr += er[i];
+        }
+        *Fa = sa / (double)N;
+        *Fr = sr / (2.0 * (double)N * (double)N);
+    }
+    free(ea); free(er);
+    return st;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Projection onto the per-shot constraint set (eq. constraints).           */
+
+/* Primal map s = pin(clip(k - D1^T q1 - D2^T q2)); q1 has Ns-1 rows, q2 Ns-2. */
+static void primal(const double *k, const double *q1, const double *q2, int Ns, double box,
+                   int pin_index, const double *pin, double *s)
+{
+    for (int m = 0; m < Ns; ++m) {
+        for (int c = 0; c < 3; ++c) {
+            double d1 = 0.0, d2 = 0.0;
+            /* (D1^T q1)[m] = q1[m-1] - q1[m] */
+            if (m - 1 >= 0 && m - 1 < Ns - 1) d1 += q1[3 * (m - 1) + c];
+            if (m < Ns - 1) d1 -= q1[3 * m + c];
+            /* (D2^T q2)[m] = q2[m-2] - 2 q2[m-1] + q2[m] */
+            if (m - 2 >= 0 && m - 2 < Ns - 2) d2 += q2[3 * (m - 2) + c];
+            if (m - 1 >= 0 && m - 1 < Ns - 2) d2 -= 2.0 * q2[3 * (m - 1) + c];
+            if (m < Ns - 2) d2 += q2[3 * m + c];
+            double v = k[3 * m + c] - d1 - d2;
+            if (v > box) v = box;
+            if (v < -box) v = -box;
+            s[3 * m + c] = v;
+        }
+    }
+    if (pin_index >= 0 && pin_index < Ns)
+        for (int c = 0; c < 3; ++c)
+            s[3 * pin_index + c] = pin[c];
+}
+
+/* z - P_{ball(radius)}(z) for one 3-vector, i.e. z * max(0, 1 - radius/|z|). */
+static void shrink(double z[3], double radius, double out[3])
+{
+    double nz = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+    double f = 0.0;
+    if (nz > radius)
+        f = 1.0 - radius / nz;
+    out[0] = z[0] * f; out[1] = z[1] * f; out[2] = z[2] * f;
+}
+
+/* Largest constraint violation of one shot: out[0] amplitude (|D1 s| - alpha)+,
+ * out[1] slew (|D2 s| - beta)+, out[2] box, out[3] pin error (max abs). */
+static void violation_one(const double *s, int Ns, double alpha, double beta, double box,
+                          int pin_index, const double *pin, double out[4])
+{
+    double v1 = 0.0, v2 = 0.0, vb = 0.0, vp = 0.0;
+    for (int n = 0; n + 1 < Ns; ++n) {
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = s[3 * (n + 1) + c] - s[3 * n + c];
+        double e = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - alpha;
+        if (e > v1) v1 = e;
+    }
+    for (int n = 0; n + 2 < Ns; ++n) {
+        double d[3];
+        for (int c = 0; c < 3; ++c)
+            d[c] = s[3 * (n + 2) + c] - 2.0 * s[3 * (n + 1) + c] + s[3 * n + c];
+        double e = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - beta;
+        if (e > v2) v2 = e;
+    }
+    for (int m = 0; m < 3 * Ns; ++m) {
+        double e = fabs(s[m]) - box;
+        if (e > vb) vb = e;
+    }
+    if (pin_index >= 0 && pin_index < Ns)
+        for (int c = 0; c < 3; ++c) {
+            double e = fabs(s[3 * pin_index + c] - pin[c]);
+            if (e > vp) vp = e;
+        }
+    out[0] = v1; out[1] = v2; out[2] = vb; out[3] = vp;
+}
+
+/* Duality gap of the dual point q at its primal image s = s(q):
+ *   gap = sum_n (alpha |q1_n| - <q1_n, D1 s_n>) + (beta |q2_n| - <q2_n, D2 s_n>).
+ * When s is feasible, 1/2 |s - s*|^2 <= gap (the primal objective is
+ * 1-strongly convex and bounded below by the dual one). */
+static double dual_gap(const double *s, const double *q1, const double *q2, int Ns, double alpha,
+                       double beta)
+{
+    double g = 0.0;
+    for (int n = 0; n + 1 < Ns; ++n) {
+        double nq = 0.0, ip = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double d = s[3 * (n + 1) + c] - s[3 * n + c];
+            nq += q1[3 * n + c] * q1[3 * n + c];
+            ip += q1[3 * n + c] * d;
+        }
+        g += alpha * sqrt(nq) - ip;
+    }
+    for (int n = 0; n + 2 < Ns; ++n) {
+        double nq = 0.0, ip = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double d = s[3 * (n + 2) + c] - 2.0 * s[3 * (n + 1) + c] + s[3 * n + c];
+            nq += q2[3 * n + c] * q2[3 * n + c];
+            ip += q2[3 * n + c] * d;
+        }
+        g += beta * sqrt(nq) - ip;
+    }
+    return g;
+}
+
+/* Converged-mode certificate: every violation of the (possibly shrunk) set
+ * and the duality gap are <= tol. */
+static int certified(const double *s, const double *q1, const double *q2, int Ns, double alpha,
+                     double beta, double box, int pin_index, const double *pin, double tol)
+{
+    double v[4];
+    violation_one(s, Ns, alpha, beta, box, pin_index, pin, v);
+    if (!(v[0] <= tol && v[1] <= tol && v[2] <= tol && v[3] <= tol))
+        return 0;
+    return dual_gap(s, q1, q2, Ns, alpha, beta) <= tol;
+}
+
+/* Dual FISTA for one shot.  Returns the iterations run; *conv is set to 1 when
+ * tol > 0 and the violation test passed (always 1 in fixed-iteration mode). */
+static int project_one(const double *k, double *s, int Ns, double alpha, double beta, double box,
+                       int pin_index, const double *pin, int n_iter, double tol, double margin,
+                       int check_every, int *conv)
+{
+    int n1 = Ns > 1 ? Ns - 1 : 0, n2 = Ns > 2 ? Ns - 2 : 0;
+    double *q1 = (double *)calloc((size_t)(3 * n1 + 3), sizeof(double));
+    double *q2 = (double *)calloc((size_t)(3 * n2 + 3), sizeof(double));
+    double *y1 = (double *)calloc((size_t)(3 * n1 + 3), sizeof(double));
+    double *y2 = (double *)calloc((size_t)(3 * n2 + 3), sizeof(double));
+    const double tau = 1.0 / 20.0;
+    /* Converged mode aims at the shrunk set so that the final iterate can be
+     * strictly inside the requested one. */
+    double a_eff = tol > 0.0 ? alpha * (1.0 - margin) : alpha;
+    double b_eff = tol > 0.0 ? beta * (1.0 - margin) : beta;
+    double t = 1.0;
+    int it = 0;
+    *conv = tol > 0.0 ? 0 : 1;
+    for (it = 0; it < n_iter; ++it) {
+        primal(k, y1, y2, Ns, box, pin_index, pin, s);
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        double mom = (t - 1.0) / tn;
+        for (int n = 0; n < n1; ++n) {
+            double z[3], qn[3];
+            for (int c = 0; c < 3; ++c)
+                z[c] = y1[3 * n + c] + tau * (s[3 * (n + 1) + c] - s[3 * n + c]);
+            shrink(z, tau * a_eff, qn);
+            for (int c = 0; c < 3; ++c) {
+                y1[3 * n + c] = qn[c] + mom * (qn[c] - q1[3 * n + c]);
+                q1[3 * n + c] = qn[c];
+            }
+        }
+        for (int n = 0; n < n2; ++n) {
+            double z[3], qn[3];
+            for (int c = 0; c < 3; ++c)
+                z[c] = y2[3 * n + c] +
+                       tau * (s[3 * (n + 2) + c] - 2.0 * s[3 * (n + 1) + c] + s[3 * n + c]);
+            shrink(z, tau * b_eff, qn);
+            for (int c = 0; c < 3; ++c) {
+                y2[3 * n + c] = qn[c] + mom * (qn[c] - q2[3 * n + c]);
+                q2[3 * n + c] = qn[c];
+            }
+        }
+        t = tn;
+        if (tol > 0.0 && check_every > 0 && (it + 1) % check_every == 0) {
+            primal(k, q1, q2, Ns, box, pin_index, pin, s);
+            if (certified(s, q1, q2, Ns, a_eff, b_eff, box, pin_index, pin, tol)) {
+                *conv = 1;
+                ++it;
+                break;
+            }
+        }
+    }
+    primal(k, q1, q2, Ns, box, pin_index, pin, s);
+    if (tol > 0.0 && !*conv)
+        *conv = certified(s, q1, q2, Ns, a_eff, b_eff, box, pin_index, pin, tol);
+    free(q1); free(q2); free(y1); free(y2);
+    return it;
+}
+
+/*
+ * Project Nc shots of Ns samples (Kin, Kout: [Nc*Ns][3], may alias).
+ * alpha/beta may be +inf (constraint off).  pin_index < 0: no pin.
+ * tol <= 0: exactly n_iter iterations.  tol > 0: aim at the set shrunk by
+ * (1 - margin) and stop at the first check (every check_every iterations)
+ * where every violation of that set and the duality gap are <= tol; returns
+ * ORACLE_ENOTCONV if a shot did not get there within n_iter.  iters_out (optional, [Nc]) receives the iterations run.
+ */
+int oracle_project(const double *Kin, double *Kout, int64_t Nc, int64_t Ns, double alpha,
+                   double beta, double box, int64_t pin_index, const double *pin, int64_t n_iter,
+                   double tol, double margin, int64_t check_every, int64_t *iters_out)
+{
+    if (!Kin || !Kout || Nc < 0 || Ns < 1 || !(alpha > 0) || !(beta > 0) || !(box > 0) ||
+        n_iter < 0 || (pin_index >= 0 && !pin))
+        return ORACLE_EINVAL;
+    int notconv = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : notconv)
+    for (int64_t c = 0; c < Nc; ++c) {
+        double *k = (double *)malloc(sizeof(double) * (size_t)(3 * Ns));
+        memcpy(k, Kin + 3 * c * Ns, sizeof(double) * (size_t)(3 * Ns));
+        int conv = 1;
+        int it = project_one(k, Kout + 3 * c * Ns, (int)Ns, alpha, beta, box, (int)pin_index, pin,
+                             (int)n_iter, tol, margin, (int)check_every, &conv);
+        if (iters_out) iters_out[c] = it;
+        if (!conv) notconv = 1;
+        free(k);
+    }
+    return notconv ? ORACLE_ENOTCONV : ORACLE_OK;
+}
+
+/* Largest violation over all shots (same four entries as violation_one). */
+int oracle_violation(const double *K, int64_t Nc, int64_t Ns, double alpha, double beta,
+                     double box, int64_t pin_index, const double *pin, double out[4])
+{
+    if (!K || Nc < 0 || Ns < 1 || (pin_index >= 0 && !pin))
+        return ORACLE_EINVAL;
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    for (int64_t c = 0; c < Nc; ++c) {
+        double v[4];
+        violation_one(K + 3 * c * Ns, (int)Ns, alpha, beta, box, (int)pin_index, pin, v);
+        for (int e = 0; e < 4; ++e)
+            if (v[e] > out[e]) out[e] = v[e];
+    }
+    return ORACLE_OK;
+}
+
+/* One projected-gradient step (eq. proj_grad_descent with the scaled gradient
+ * G = N dF/dK): K <- Pi(K - eta G), in place, K is [Nc*Ns][3]. */
+int oracle_step(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_t nx, int64_t ny,
+                int64_t nz, double lo, double hi, double eta, double alpha, double beta, double box,
+                int64_t pin_index, const double *pin, int64_t n_iter)
+{
+    int64_t N = Nc * Ns;
+    double *G = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    if (!G) return ORACLE_EINVAL;
+    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, G, NULL, NULL);
+    if (st == ORACLE_OK) {
+        for (int64_t m = 0; m < 3 * N; ++m)
+            G[m] = K[m] - eta * G[m];
+        st = oracle_project(G, K, Nc, Ns, alpha, beta, box, pin_index, pin, n_iter, 0.0, 0.0, 0,
+                            NULL);
+    }
+    free(G);
+    return st;
+}
