@@ -1,0 +1,221 @@
+/*
+ * sparkling.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * full-3D SPARKLING (arxiv 2108.02991): the gradient and energy of the
+ * attraction-repulsion cost with kernel H(x) = |x|_2, and the per-shot
+ * projection onto the gradient-amplitude and slew-rate constraints.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Samples K are N = Nc * Ns points in [-1/2,1/2]^3 (the paper's Omega =
+ *   [-1,1]^3 of Sec. II-A scaled by 1/2), stored shot after shot as an
+ *   array-of-structs [N][3] of float (SPARKLING_F32) or double (SPARKLING_F64).
+ * - The target density is sampled on a cell-centred grid: along an axis of n
+ *   cells over [lo, hi] the points are lo + (q + 1/2)(hi - lo)/n, q = 0..n-1.
+ *   rho is float32, C order [nz][ny][nx] (x fastest), rho >= 0; the sum is
+ *   expected to be 1 (eq. discritize with the integral replaced by a sum) but
+ *   is not enforced.
+ * - Array arguments are DEVICE pointers (cudaMalloc or managed memory) owned
+ *   by the caller unless the name ends in _host.  The library never frees them.
+ *   A pointer the CUDA runtime does not report as device or managed memory is
+ *   rejected with SPARKLING_E_INVAL before anything is launched.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on it unless they return a host value (those block
+ *   on `stream` before returning).
+ * - Each context owns its device workspace.  It grows on demand: the library
+ *   synchronises the device, frees the old buffer and cudaMallocs a larger
+ *   one (SPARKLING_E_NOMEM if that fails).  Call once at the largest size
+ *   before capturing a CUDA graph.  A context is not thread-safe; use one per
+ *   host thread.
+ * - Arguments are validated before any launch; a failing check returns
+ *   SPARKLING_E_INVAL and sparkling_last_error() says which.  No C++ exception
+ *   crosses the ABI.
+ * - Errors found on the device (non-finite input, a bounded wait that ran out)
+ *   are recorded in a device status word of the context.  Blocking calls
+ *   return them; after asynchronous calls, sparkling_status() reports them.
+ *
+ * Notation (paper Sec. II-B/II-C, eqs. attraction_term, repulsion_term,
+ * attraction_derivative_basic, Fr_grad with H = |.|_2, H' = 1):
+ *   A_i = sum_q rho_q (K_i - x_q) / |K_i - x_q|           attraction force
+ *   R_i = (1/N) sum_{j != i} (K_i - K_j) / |K_i - K_j|    repulsion force
+ *   G_i = A_i - R_i = N * dF/dK_i                         the "gradient"
+ *   F   = F^a - F^r,  F^a = (1/N) sum_i sum_q rho_q |K_i - x_q|,
+ *                     F^r = (1/(2 N^2)) sum_{i != j} |K_i - K_j|
+ * A pair whose distance is (numerically) zero contributes nothing.
+ */
+#ifndef SPARKLING_H
+#define SPARKLING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(_WIN32)
+#define SPARKLING_API
+#else
+#define SPARKLING_API __attribute__((visibility("default")))
+#endif
+
+/* Status codes returned by every int-valued entry point. */
+#define SPARKLING_OK 0
+#define SPARKLING_E_INVAL 1     /* bad argument; nothing was launched */
+#define SPARKLING_E_NOMEM 2     /* workspace allocation failed */
+#define SPARKLING_E_CUDA 3      /* a CUDA runtime call failed (no device, launch error...) */
+#define SPARKLING_E_NONFINITE 4 /* NaN/Inf in K or rho, or negative rho */
+#define SPARKLING_E_TIMEOUT 5   /* a bounded device wait gave up (the kernel returned early) */
+#define SPARKLING_E_NOTCONV 6   /* converged-mode projection did not certify within n_iter */
+
+/* Element types of K, G, A, R. */
+#define SPARKLING_F32 0
+#define SPARKLING_F64 1
+
+/* Per-target accumulation of the FP32 pair sums.
+ * KAHAN32: every grid row / source block is summed in FP32 and folded into a
+ *          compensated (TwoSum) FP32 accumulator.
+ * FP64:    the same FP32 partial sums are folded into FP64 accumulators. */
+#define SPARKLING_ACC_KAHAN32 0
+#define SPARKLING_ACC_FP64 1
+
+typedef struct sparkling_ctx sparkling_ctx;
+
+/* Density grid (eq. discritize): device pointer rho [nz][ny][nx] float32 on
+ * the cell-centred grid over [lo, hi]^3 described above.  1 <= n[a] and
+ * n[0] (= nx) <= 4096. */
+typedef struct sparkling_grid {
+    const float *rho;
+    double lo;
+    double hi;
+    int32_t n[3]; /* nx, ny, nz */
+    int32_t reserved;
+} sparkling_grid;
+
+/* Constraint set of one shot (eq. constraints): |s|_inf <= box,
+ * |s[n+1]-s[n]|_2 <= alpha, |s[n+2]-2s[n+1]+s[n]|_2 <= beta for every n, and
+ * s[pin_index] = pin (the linear constraint A k = v; pin_index < 0: none).
+ * alpha or beta = +inf switches that constraint off.
+ * tol <= 0: exactly n_iter dual-FISTA iterations.  tol > 0 ("converged
+ * mode"): aim at the set with alpha, beta shrunk by (1 - margin) and stop at
+ * the first check (every check_every iterations) where all violations of that
+ * set and the duality gap are <= tol. */
+typedef struct sparkling_proj {
+    double alpha;
+    double beta;
+    double box;
+    double tol;
+    double margin;
+    double pin[3];
+    int32_t pin_index;
+    int32_t n_iter;
+    int32_t check_every;
+    int32_t reserved;
+} sparkling_proj;
+
+/* Kernel kinds reported by sparkling_kernel_times(). */
+#define SPARKLING_KERNEL_PACK 0
+#define SPARKLING_KERNEL_ATTRACTION 1
+#define SPARKLING_KERNEL_REPULSION 2
+#define SPARKLING_KERNEL_COMBINE 3
+#define SPARKLING_KERNEL_PROJECT 4
+#define SPARKLING_KERNEL_COUNT 5
+
+/* Create a context bound to CUDA device `device`.  Nothing is allocated on
+ * the device and no CUDA call is made until the first compute call.
+ * Returns SPARKLING_E_INVAL if out is NULL or device < 0. */
+SPARKLING_API int sparkling_create(sparkling_ctx **out, int device);
+
+/* Release the context and its workspace (synchronises the device first).
+ * NULL is ignored. */
+SPARKLING_API void sparkling_destroy(sparkling_ctx *ctx);
+
+/* Message of the last failure on this context (ctx == NULL: of the last
+ * failure with no context on this thread).  Never NULL; owned by the library,
+ * valid until the next call on the same context/thread. */
+SPARKLING_API const char *sparkling_last_error(const sparkling_ctx *ctx);
+
+/* Attraction-repulsion gradient (Sec. II-C, eqs. attraction_derivative_basic
+ * and Fr_grad; the attraction is the direct sum over the density grid).
+ *   K       [N][3] of K_dtype, N >= 2 (read only)
+ *   grid    density grid (struct in host memory, rho on the device)
+ *   acc     SPARKLING_ACC_KAHAN32 or SPARKLING_ACC_FP64
+ *   G       [N][3] of G_dtype, receives A - R
+ *   A, R    optional [N][3] of G_dtype (NULL: not written), receive A and R
+ * Asynchronous on `stream`. */
+SPARKLING_API int sparkling_grad(sparkling_ctx *ctx, const void *K, int K_dtype, int64_t N,
+                                 const sparkling_grid *grid, int acc, void *G, int G_dtype,
+                                 void *A, void *R, void *stream);
+
+/* Energy F = F^a - F^r (eqs. global_minimization, attraction_term,
+ * repulsion_term).  Same K, grid, acc as sparkling_grad.  Writes the three
+ * host doubles (any may be NULL) and blocks on `stream`.  The per-target sums
+ * are reduced in a fixed order, so repeated calls give identical results. */
+SPARKLING_API int sparkling_energy(sparkling_ctx *ctx, const void *K, int K_dtype, int64_t N,
+                                   const sparkling_grid *grid, int acc, double *F_host,
+                                   double *Fa_host, double *Fr_host, void *stream);
+
+/* Backward of sparkling_energy for automatic differentiation: writes
+ *   dK = g * dF/dK = g * (A - R) / N,   g = scale * (*g_dev)  (g_dev NULL: 1)
+ * where g_dev is a device pointer to one double (the upstream gradient of
+ * the energy).  dK is [N][3] of dK_dtype on the device.  The per-pair
+ * distances are recomputed, never stored.  Asynchronous on `stream`. */
+SPARKLING_API int sparkling_energy_backward(sparkling_ctx *ctx, const void *K, int K_dtype,
+                                            int64_t N, const sparkling_grid *grid, int acc,
+                                            const double *g_dev, double scale, void *dK,
+                                            int dK_dtype, void *stream);
+
+/* Projection of each of Nc shots of Ns samples onto the constraint set
+ * (Sec. II-D, Suppl. Sec. I), in place on K ([Nc*Ns][3], K_dtype), with the
+ * dual FISTA iteration in FP64:
+ *   D1 s[n] = s[n+1]-s[n], D2 s[n] = s[n+2]-2s[n+1]+s[n];
+ *   s(q) = pin(clip_box(k - D1^T q1 - D2^T q2)); step tau = 1/20;
+ *   z = y + tau D s(y); q+ = z - P_ball(tau*alpha or tau*beta)(z) per row;
+ *   t+ = (1 + sqrt(1 + 4t^2))/2; y = q+ + ((t-1)/t+)(q+ - q);
+ *   output s(q) (q = y = 0, t = 1 at the start of every call).
+ * Nc >= 1, 1 <= Ns <= 65536.  viol_host (optional, [4]) receives the largest
+ * amplitude, slew, box and pin violation of the result; when it is given, or
+ * in converged mode, the call blocks on `stream`. */
+SPARKLING_API int sparkling_project(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc,
+                                    int64_t Ns, const sparkling_proj *proj, double *viol_host,
+                                    void *stream);
+
+/* One projected-gradient step (eq. proj_grad_descent, Algorithm 1 inner
+ * loop): K <- Pi(K - eta * G(K)) in place, G = A - R as in sparkling_grad
+ * (so eta = 1/N is a unit step on dF/dK).  The gradient is kept in FP64 in
+ * the workspace; the step and the projection run in FP64 and the result is
+ * rounded to K_dtype.  Asynchronous unless converged mode is requested. */
+SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns,
+                                 const sparkling_grid *grid, int acc, double eta,
+                                 const sparkling_proj *proj, void *stream);
+
+/* sparkling_step on HOST buffers: K_host [Nc*Ns][3] (K_dtype) is copied to
+ * the device, stepped, and copied back; rho_host [nz][ny][nx] float32 is
+ * copied to the device (grid->rho is ignored).  Blocks until K_host holds
+ * the result.  Pinned host memory makes the copies asynchronous DMA. */
+SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dtype, int64_t Nc,
+                                      int64_t Ns, const sparkling_grid *grid,
+                                      const float *rho_host, int acc, double eta,
+                                      const sparkling_proj *proj, void *stream);
+
+/* Synchronise `stream`, then return and clear the device status word of the
+ * context (SPARKLING_OK, SPARKLING_E_NONFINITE or SPARKLING_E_TIMEOUT). */
+SPARKLING_API int sparkling_status(sparkling_ctx *ctx, void *stream);
+
+/* Kernel timing: when enabled, every kernel launch of the context is
+ * bracketed by CUDA events on its stream.  sparkling_kernel_times()
+ * synchronises the pending events and writes, for the first n kinds
+ * (SPARKLING_KERNEL_*), the total milliseconds and the number of launches
+ * since the last reset; reset != 0 clears the totals afterwards. */
+SPARKLING_API int sparkling_set_timing(sparkling_ctx *ctx, int enable);
+SPARKLING_API int sparkling_kernel_times(sparkling_ctx *ctx, double *ms_out, int64_t *launches_out,
+                                         int n, int reset);
+
+/* Number of kernels this context has launched since it was created. */
+SPARKLING_API int64_t sparkling_launch_count(const sparkling_ctx *ctx);
+
+/* Library version string, e.g. "sparkling-gb300 0.1 sm_103a". */
+SPARKLING_API const char *sparkling_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARKLING_H */

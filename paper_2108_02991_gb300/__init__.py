@@ -1,0 +1,290 @@
+"""Python binding of libsparkling.so, the GB300 (sm_103a) library for the hot
+path of full-3D SPARKLING (arxiv 2108.02991).
+
+This module only marshals arguments: every function calls the C entry point
+of the same name (declared in include/sparkling.h) with device pointers taken
+from torch tensors and the current torch stream.  There is no fallback: if the
+shared library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsparkling.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV = range(7)
+F32, F64 = 0, 1
+ACC_KAHAN32, ACC_FP64 = 0, 1
+KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project")
+
+# Every entry point declared in include/sparkling.h.
+ABI_SYMBOLS = (
+    "sparkling_create", "sparkling_destroy", "sparkling_last_error", "sparkling_grad",
+    "sparkling_energy", "sparkling_energy_backward", "sparkling_project", "sparkling_step",
+    "sparkling_step_host", "sparkling_status", "sparkling_set_timing", "sparkling_kernel_times",
+    "sparkling_launch_count", "sparkling_version",
+)
+
+
+class SparklingError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    """sparkling_grid: rho device pointer, lo, hi, n = (nx, ny, nz)."""
+    _fields_ = [("rho", ctypes.c_void_p), ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+                ("n", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+
+
+class Proj(ctypes.Structure):
+    """sparkling_proj: constraint set and iteration control of the projection."""
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("box", ctypes.c_double),
+                ("tol", ctypes.c_double), ("margin", ctypes.c_double),
+                ("pin", ctypes.c_double * 3), ("pin_index", ctypes.c_int32),
+                ("n_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsparkling.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with paper_2108_02991_gb300.build.build() "
+                "(or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "sparkling_create": ([ctypes.POINTER(p), i], i),
+            "sparkling_destroy": ([p], None),
+            "sparkling_last_error": ([p], ctypes.c_char_p),
+            "sparkling_grad": ([p, p, i, i64, ctypes.POINTER(Grid), i, p, i, p, p, p], i),
+            "sparkling_energy": ([p, p, i, i64, ctypes.POINTER(Grid), i, p, p, p, p], i),
+            "sparkling_energy_backward": ([p, p, i, i64, ctypes.POINTER(Grid), i, p, d, p, i, p], i),
+            "sparkling_project": ([p, p, i, i64, i64, ctypes.POINTER(Proj), p, p], i),
+            "sparkling_step": ([p, p, i, i64, i64, ctypes.POINTER(Grid), i, d, ctypes.POINTER(Proj), p], i),
+            "sparkling_step_host": ([p, p, i, i64, i64, ctypes.POINTER(Grid), p, i, d,
+                                     ctypes.POINTER(Proj), p], i),
+            "sparkling_status": ([p, p], i),
+            "sparkling_set_timing": ([p, i], i),
+            "sparkling_kernel_times": ([p, p, p, i, i], i),
+            "sparkling_launch_count": ([p], i64),
+            "sparkling_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib_handle = L
+    return _lib_handle
+
+
+def _check(ctx, code: int):
+    if code != OK:
+        msg = lib().sparkling_last_error(ctx.handle if ctx is not None else None)
+        raise SparklingError(code, msg.decode() if msg else "unknown error")
+
+
+class Context:
+    """Owns a sparkling_ctx (device workspace, timing state)."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        code = lib().sparkling_create(ctypes.byref(h), int(device))
+        if code != OK:
+            raise SparklingError(code, lib().sparkling_last_error(None).decode())
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sparkling_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sparkling_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def sparkling_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def sparkling_last_error(ctx: Optional[Context] = None) -> str:
+    return lib().sparkling_last_error(ctx.handle if ctx else None).decode()
+
+
+def sparkling_version() -> str:
+    return lib().sparkling_version().decode()
+
+
+# --- marshalling helpers ----------------------------------------------------
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"expected float32 or float64, got {t.dtype}")
+
+
+def _dev_ptr(t, what: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_grid(rho, lo: float = -0.5, hi: float = 0.5, n: Optional[Sequence[int]] = None) -> Grid:
+    """sparkling_grid for a float32 density tensor [nz, ny, nx] (device or,
+    for the host entry points, any) -- n defaults to rho's shape."""
+    if n is None:
+        nz, ny, nx = rho.shape
+        n = (nx, ny, nz)
+    g = Grid()
+    g.rho = ctypes.c_void_p(rho.data_ptr()) if (rho is not None and rho.is_cuda) else None
+    g._rho_ref = rho        # the struct holds a raw pointer: keep the tensor alive with it
+    g.lo, g.hi = float(lo), float(hi)
+    for a in range(3):
+        g.n[a] = int(n[a])
+    return g
+
+
+def make_proj(alpha, beta, box=0.5, n_iter=100, pin_index=-1, pin=(0.0, 0.0, 0.0), tol=0.0,
+              margin=0.0, check_every=10) -> Proj:
+    p = Proj()
+    p.alpha, p.beta, p.box = float(alpha), float(beta), float(box)
+    p.tol, p.margin = float(tol), float(margin)
+    for c in range(3):
+        p.pin[c] = float(pin[c])
+    p.pin_index, p.n_iter, p.check_every = int(pin_index), int(n_iter), int(check_every)
+    return p
+
+
+def _rows(K) -> int:
+    if K.dim() != 2 or K.shape[1] != 3:
+        raise ValueError("K must have shape [N, 3]")
+    return int(K.shape[0])
+
+
+# --- entry points -------------------------------------------------------------
+
+def sparkling_grad(ctx: Context, K, grid: Grid, acc: int = ACC_KAHAN32, G=None, A=None, R=None,
+                   stream=None):
+    """G = A - R for every sample (asynchronous); returns G."""
+    import torch
+    N = _rows(K)
+    if G is None:
+        G = torch.empty_like(K)
+    _check(ctx, lib().sparkling_grad(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), N,
+                                     ctypes.byref(grid), acc, _dev_ptr(G, "G"), _dtype_code(G),
+                                     _dev_ptr(A, "A"), _dev_ptr(R, "R"), _stream(stream)))
+    return G
+
+
+def sparkling_energy(ctx: Context, K, grid: Grid, acc: int = ACC_KAHAN32, stream=None):
+    """(F, F^a, F^r) as Python floats (blocks on the stream)."""
+    F, Fa, Fr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().sparkling_energy(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), _rows(K),
+                                       ctypes.byref(grid), acc, ctypes.byref(F), ctypes.byref(Fa),
+                                       ctypes.byref(Fr), _stream(stream)))
+    return F.value, Fa.value, Fr.value
+
+
+def sparkling_energy_backward(ctx: Context, K, grid: Grid, g=None, scale: float = 1.0,
+                              acc: int = ACC_KAHAN32, dK=None, stream=None):
+    """dK = scale * g * (A - R) / N with g a float64 device scalar tensor (or None)."""
+    import torch
+    if dK is None:
+        dK = torch.empty_like(K)
+    if g is not None and g.dtype != torch.float64:
+        raise TypeError("g must be a float64 tensor")
+    _check(ctx, lib().sparkling_energy_backward(
+        ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), _rows(K), ctypes.byref(grid), acc,
+        _dev_ptr(g, "g"), float(scale), _dev_ptr(dK, "dK"), _dtype_code(dK), _stream(stream)))
+    return dK
+
+
+def sparkling_project(ctx: Context, K, Nc: int, Ns: int, proj: Proj, want_violation: bool = False,
+                      stream=None):
+    """Project every shot of K in place; returns the (amplitude, slew, box,
+    pin) violations of the result when asked (blocks then)."""
+    v = (ctypes.c_double * 4)() if want_violation else None
+    _check(ctx, lib().sparkling_project(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), int(Nc),
+                                        int(Ns), ctypes.byref(proj), v, _stream(stream)))
+    return list(v) if want_violation else None
+
+
+def sparkling_step(ctx: Context, K, Nc: int, Ns: int, grid: Grid, eta: float, proj: Proj,
+                   acc: int = ACC_KAHAN32, stream=None):
+    """K <- Pi(K - eta G) in place (asynchronous unless converged mode)."""
+    _check(ctx, lib().sparkling_step(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), int(Nc),
+                                     int(Ns), ctypes.byref(grid), acc, float(eta),
+                                     ctypes.byref(proj), _stream(stream)))
+
+
+def sparkling_step_host(ctx: Context, K_host, Nc: int, Ns: int, grid: Grid, rho_host, eta: float,
+                        proj: Proj, acc: int = ACC_KAHAN32, stream=None):
+    """sparkling_step on host tensors (CPU, contiguous; pinned for async DMA)."""
+    for t, what in ((K_host, "K_host"), (rho_host, "rho_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous host tensor")
+    _check(ctx, lib().sparkling_step_host(ctx.handle, ctypes.c_void_p(K_host.data_ptr()),
+                                          _dtype_code(K_host), int(Nc), int(Ns), ctypes.byref(grid),
+                                          ctypes.c_void_p(rho_host.data_ptr()), acc, float(eta),
+                                          ctypes.byref(proj), _stream(stream)))
+
+
+def sparkling_status(ctx: Context, stream=None) -> int:
+    """Synchronise and raise if the device recorded an error since the last check."""
+    code = lib().sparkling_status(ctx.handle, _stream(stream))
+    _check(ctx, code)
+    return code
+
+
+def sparkling_set_timing(ctx: Context, enable: bool = True) -> None:
+    _check(ctx, lib().sparkling_set_timing(ctx.handle, 1 if enable else 0))
+
+
+def sparkling_kernel_times(ctx: Context, reset: bool = False):
+    """{kernel kind: (total ms, launches)} since the last reset."""
+    n = len(KERNEL_NAMES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(ctx, lib().sparkling_kernel_times(ctx.handle, ms, cnt, n, 1 if reset else 0))
+    return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def sparkling_launch_count(ctx: Context) -> int:
+    return int(lib().sparkling_launch_count(ctx.handle))
+
+
+from .autograd import SparklingEnergy, sparkling_energy_fn  # noqa: E402,F401
