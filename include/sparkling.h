@@ -196,6 +196,32 @@ SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dt
                                       const float *rho_host, int acc, double eta,
                                       const sparkling_proj *proj, void *stream);
 
+/* The gradient of sparkling_grad without any device allocation, for callers
+ * that must not (or cannot) let a library call cudaMalloc: processes whose
+ * device memory belongs to their own pool or arena, code that must not
+ * trigger the synchronisation or failure modes of a new allocation, and
+ * deployments that need every byte a library holds known in advance.  The
+ * paper has no counterpart; this is an engineering variant of the gradient.
+ *
+ * No context: scratch space is one fixed array compiled into the library,
+ * 32 MiB, held on every GPU that loads the library until the process exits.
+ * A problem needs about 16 N + 4 ny nz ceil4(nx) bytes plus at least 128 KiB
+ * per 1024 samples of partial sums (more when the GPU has CTAs to spare); sizes that
+ * do not fit are rejected with SPARKLING_E_INVAL and a message giving the
+ * bytes needed (e.g. N up to ~2e5 with a 64^3 grid fits).  K, G and
+ * grid->rho are device memory as in sparkling_grad; G = A - R in G_dtype.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before capturing any CUDA stream.  All calls share the array;
+ * each call clears its status word and overwrites every other byte it reads,
+ * but calls whose kernels overlap on the GPU race on it and must be
+ * serialised by the caller.  Blocks on `stream` and returns device-side
+ * errors (SPARKLING_E_NONFINITE, SPARKLING_E_TIMEOUT) directly; messages go
+ * to sparkling_last_error(NULL). */
+SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, int64_t N,
+                                         const sparkling_grid *grid, int acc, void *G, int G_dtype,
+                                         void *stream);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * context (SPARKLING_OK, SPARKLING_E_NONFINITE or SPARKLING_E_TIMEOUT). */
 SPARKLING_API int sparkling_status(sparkling_ctx *ctx, void *stream);

@@ -25,7 +25,7 @@ ABI_SYMBOLS = (
     "sparkling_create", "sparkling_destroy", "sparkling_last_error", "sparkling_grad",
     "sparkling_energy", "sparkling_energy_backward", "sparkling_project", "sparkling_step",
     "sparkling_step_host", "sparkling_status", "sparkling_set_timing", "sparkling_kernel_times",
-    "sparkling_launch_count", "sparkling_version",
+    "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
 )
 
 
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "sparkling_kernel_times": ([p, p, p, i, i], i),
             "sparkling_launch_count": ([p], i64),
             "sparkling_version": ([], ctypes.c_char_p),
+            "sparkling_grad_noalloc": ([p, i, i64, ctypes.POINTER(Grid), i, p, i, p], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -207,6 +208,20 @@ def sparkling_grad(ctx: Context, K, grid: Grid, acc: int = ACC_KAHAN32, G=None, 
     _check(ctx, lib().sparkling_grad(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), N,
                                      ctypes.byref(grid), acc, _dev_ptr(G, "G"), _dtype_code(G),
                                      _dev_ptr(A, "A"), _dev_ptr(R, "R"), _stream(stream)))
+    return G
+
+
+def sparkling_grad_noalloc(K, grid: Grid, acc: int = ACC_KAHAN32, G=None, stream=None):
+    """G = A - R using only the library's fixed 32 MiB scratch array (no
+    device allocation by the library; blocks on the stream).  For callers
+    whose device memory is owned by their own pool or budget."""
+    import torch
+    N = _rows(K)
+    if G is None:
+        G = torch.empty_like(K)
+    _check(None, lib().sparkling_grad_noalloc(_dev_ptr(K, "K"), _dtype_code(K), N,
+                                              ctypes.byref(grid), acc, _dev_ptr(G, "G"),
+                                              _dtype_code(G), _stream(stream)))
     return G
 
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparkling.so")
-SOURCES = ["api.cu", "pairs.cu", "project.cu"]
+SOURCES = ["api.cu", "pairs.cu", "project.cu", "noalloc.cu"]
 HEADERS = ["kernels.h", "ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

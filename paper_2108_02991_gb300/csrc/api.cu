@@ -427,6 +427,10 @@ int check_shots(sparkling_ctx *ctx, int64_t Nc, int64_t Ns)
 
 } // namespace
 
+// Lets other translation units of the library (noalloc.cu) report a failure
+// through sparkling_last_error(NULL).
+void sparkling_set_thread_error(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 SPARKLING_API int sparkling_create(sparkling_ctx **out, int device)
