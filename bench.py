@@ -14,7 +14,7 @@ Default workload: 4096 shots x 2560 samples = 10,485,760 samples, density
 grid 256^3 = 16,777,216 points (the ~1e7-sample configuration).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload hr|diff|medium|tiny] [--acc kahan|fp64]
+                  [--workload hr|diff|medium|small|tiny] [--acc kahan|fp64]
 
 Under torchrun (N > 1) every rank runs an independent problem instance of
 the same size (its own seed) on its own GPU: the trajectories are
@@ -36,7 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
-SFU_RSQ_PER_SM_CLK = 16         # MUFU.RSQ results per SM per clock (measured, profiles/)
+SFU_RSQ_PER_SM_CLK = 16         # MUFU.RSQ results per SM per clock on GB300 (alu_peak_probe.cu)
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -48,7 +48,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hr", "diff", "medium", "tiny"), default="hr")
+    ap.add_argument("--workload", choices=("hr", "diff", "medium", "small", "tiny"), default="hr")
     ap.add_argument("--acc", choices=("kahan", "fp64"), default="kahan")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -153,6 +153,27 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def measure_rsq_rate():
+    """Run alu_peak_probe.cu (built with nvcc) and return the measured
+    MUFU.RSQ results per SM per clock, or None when it cannot run."""
+    import re
+    import shutil
+    import tempfile
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = os.path.join(ROOT, "alu_peak_probe.cu")
+    if not (os.path.exists(nvcc) and os.path.exists(src)):
+        return None
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "probe")
+        r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                            src], capture_output=True, text=True)
+        if r.returncode != 0:
+            return None
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    m = re.search(r"^rsqrt\s+ops/SM/clk = ([0-9.]+)", r.stdout, re.M)
+    return float(m.group(1)) if m else None
 
 
 # --- oracle timing (the CPU baseline and the reference arm) -------------------
@@ -293,15 +314,18 @@ def run_ours(args):
     rep_ms, rep_n = ktimes["repulsion"]
     att_pairs = N * P
     achieved = att_pairs / (att_ms / att_n * 1e-3) if att_n else None
-    peak = sms * SFU_RSQ_PER_SM_CLK * max_mhz * 1e6
+    rsq = measure_rsq_rate() if rank == 0 else None
+    rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
+    peak = sms * rate * max_mhz * 1e6
     roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak / 1e9, "unit": "Gpair/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
             "kernel": "attraction",
-            "peak_basis": f"{sms} SMs x {SFU_RSQ_PER_SM_CLK} MUFU.RSQ/clk x {max_mhz:.0f} MHz "
-                          "(one reciprocal square root per pair)"}
+            "peak_basis": f"{sms} SMs x {rate:g} MUFU.RSQ/clk/SM x {max_mhz:.0f} MHz max SM clock "
+                          f"(one reciprocal square root per pair; probe measured "
+                          f"{rsq if rsq else 'n/a'} RSQ/clk/SM)"}
     if clk and achieved:
-        roof["frac_at_measured_clock"] = achieved / (sms * SFU_RSQ_PER_SM_CLK * clk["sm_mhz"] * 1e6)
+        roof["frac_at_measured_clock"] = achieved / (sms * rate * clk["sm_mhz"] * 1e6)
     kernels = {k: {"ms_total": round(ms, 3), "launches": n,
                    "share": round(ms / max(sum(v[0] for v in ktimes.values()), 1e-9), 4)}
                for k, (ms, n) in ktimes.items()}

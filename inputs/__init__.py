@@ -36,7 +36,7 @@ __all__ = [
     "density_gaussian", "make_problem", "make_batched", "CONFIG_NAMES",
 ]
 
-CONFIG_NAMES = ("tiny", "medium", "diff", "batched", "hr")
+CONFIG_NAMES = ("tiny", "small", "medium", "diff", "batched", "hr")
 
 
 @dataclasses.dataclass
@@ -163,8 +163,13 @@ def make_problem(name: str, seed: int = 0) -> Problem:
         grid = density_inverse_power(32, 2.0)
         return Problem(name, K, nc, ns, grid, Proj(a, b), 1.0 / (nc * ns), 1,
                        "16x64 uniform in [-1/2,1/2]^3 (f64); rho ~ 1/max(|x|,1/32)^2 on 32^3")
-    if name in ("medium", "diff", "hr"):
-        if name == "medium":
+    if name in ("small", "medium", "diff", "hr"):
+        if name == "small":
+            # a representative case small enough for detailed profiler captures
+            nc, ns, dtype = 64, 1024, np.float32
+            grid = density_inverse_power(64, 2.0)
+            iters = 1
+        elif name == "medium":
             nc, ns, dtype = 512, 512, np.float32
             grid = density_gaussian(128, 0.15, 0.05)
             iters = 10

@@ -1,0 +1,72 @@
+"""Host-side logic of bench.py on the CPU: argument defaults, the pair
+count, the max/sum-over-ranks timing reductions with two gloo ranks, and the
+reference arm (the FP64 oracle timed on the host cores) on a tiny workload."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def test_defaults_and_pair_count():
+    a = bench.parse_args([])
+    assert (a.gpus, a.workload, a.warmup, a.steps, a.impl) == (1, "hr", 3, 1, "ours")
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--warmup", "2"])
+    assert bench.pairs_per_step(10, 7) == 10 * 7 + 10 * 9
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mx = bench.reduce_max(float(rank + 1))
+    sm = bench.reduce_sum(float(10 * (rank + 1)))
+    bench.barrier()
+    out.put((rank, mx, sm))
+    dist.destroy_process_group()
+
+
+def test_two_rank_reductions_with_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 2.0, 30.0), (1, 2.0, 30.0)]
+
+
+def test_reference_arm_prints_one_line_on_rank0_only():
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+           "tiny", "--steps", "1", "--warmup", "3", "--cpu-seconds", "0.2"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
