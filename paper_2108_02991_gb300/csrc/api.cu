@@ -287,6 +287,8 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     aa.tgt = pos; aa.N = P.N; aa.rho = rho; aa.coords = coords;
     aa.gxp = P.gxp; aa.ny = P.ny; aa.nz = P.nz;
     aa.rows_per_stage = kStageFloats / P.gxp;
+    aa.hx = (float)((g->hi - g->lo) / P.nx);
+    aa.x0 = g->lo + 0.5 * ((g->hi - g->lo) / P.nx);
     aa.sp = P.spa; aa.part = at<dacc4>(ctx, P.o_parta); aa.status = ctx->d_status;
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_ATTRACTION, st);

@@ -71,6 +71,8 @@ struct AttrArgs {
     const float *coords;  // xs[gxp], ys[ny], zs[nz] (cell centres, rounded to float)
     int gxp, ny, nz;
     int rows_per_stage;
+    double x0;            // lo + h/2: x coordinate of grid column 0
+    float hx;             // grid spacing along x (columns are x0 + q hx)
     Split sp;             // per_tile = ny*nz rows
     dacc4 *part;        // [tiles][slots][kTile] (x, y, z, energy)
     int *status;

@@ -199,6 +199,8 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     AttrArgs aa;
     aa.tgt = pos; aa.N = N; aa.rho = rho; aa.coords = coords;
     aa.gxp = gxp; aa.ny = ny; aa.nz = nz; aa.rows_per_stage = kStageFloats / gxp;
+    aa.hx = (float)((grid->hi - grid->lo) / nx);
+    aa.x0 = grid->lo + 0.5 * ((grid->hi - grid->lo) / nx);
     aa.sp = spa; aa.part = part_a; aa.status = status;
     NA_CK(launch_attraction(aa, acc, false, st));
     RepArgs ra;

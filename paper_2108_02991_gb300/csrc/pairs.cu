@@ -92,36 +92,135 @@ __device__ void drain_stages(uint64_t *bars, uint32_t first, uint32_t count, int
     __syncthreads();
 }
 
-template <bool ENERGY>
-__device__ __forceinline__ void attr_pair(float kx, float s2, float x, float w_rho, float &sw,
-                                          float &sx)
+// Per-thread accumulators in shared memory, one column per thread (a warp
+// touches consecutive words).  ACC 0: compensated FP32 (value + TwoSum error
+// term); ACC 1: FP64.  Both take 8 bytes per accumulated value.
+template <int ACC> struct SmemAcc;
+
+template <> struct SmemAcc<0> {
+    float *p;
+    __device__ SmemAcc(void *base, int tid) : p(static_cast<float *>(base) + tid) {}
+    __device__ void zero(int nv)
+    {
+        for (int v = 0; v < 2 * nv; ++v) p[v * kThreads] = 0.f;
+    }
+    __device__ __forceinline__ void add(int v, float x)
+    {
+        float s = p[(2 * v) * kThreads], c = p[(2 * v + 1) * kThreads], t, e;
+        two_sum(s, x, t, e);
+        p[(2 * v) * kThreads] = t;
+        p[(2 * v + 1) * kThreads] = c + e;
+    }
+    __device__ double value(int v) const
+    {
+        return (double)p[(2 * v) * kThreads] + (double)p[(2 * v + 1) * kThreads];
+    }
+};
+
+template <> struct SmemAcc<1> {
+    double *p;
+    __device__ SmemAcc(void *base, int tid) : p(static_cast<double *>(base) + tid) {}
+    __device__ void zero(int nv)
+    {
+        for (int v = 0; v < nv; ++v) p[v * kThreads] = 0.0;
+    }
+    __device__ __forceinline__ void add(int v, float x) { p[v * kThreads] += (double)x; }
+    __device__ double value(int v) const { return p[v * kThreads]; }
+};
+
+constexpr int kAccBytes = kTargetsPerThread * 3 * 8 * kThreads;   // 24 KB per CTA
+
+// NR grid rows (1 or 2) against the thread's T targets.  The rows share the
+// x coordinates, so one dx = kx - x_q feeds NR pairs.  x_q is rebuilt as
+// lo + (q + 1/2) h: kxp = kx - lo - h/2 (rounded once from double) and
+// dx = kxp - q h with one FFMA per group of 4 points.  Row sums are FP32 and
+// are added into the stage accumulators st[t][0..NV).
+template <bool ENERGY, int NR>
+__device__ __forceinline__ void attr_rows(const float *rows, int gxp, const float *kxp,
+                                          const float *ky, const float *kz, const float *yr,
+                                          const float *zr, float h, float (*st)[3])
 {
-    const float dx = kx - x;
-    const float r2 = fmaf(dx, dx, s2);
-    const float w = w_rho * rsqrt_sfu(r2);
-    if (ENERGY) {
-        sw = fmaf(w, r2, sw);            // rho * |d|
-    } else {
-        sw += w;
-        sx = fmaf(w, dx, sx);
+    constexpr int T = kTargetsPerThread;
+    float s2[NR][T], sw[NR][T], sx[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const float dy = ky[t] - yr[r], dz = kz[t] - zr[r];
+            s2[r][t] = fmaf(dy, dy, fmaf(dz, dz, kEps2));
+            sw[r][t] = 0.f;
+        }
+        sx[t] = 0.f;
+    }
+    const float mh = -h, h2 = 2.f * h, h3 = 3.f * h;
+    const int n4 = gxp >> 2;
+    float qf = 0.f;
+#pragma unroll (NR == 1 ? 2 : 1)
+    for (int g4 = 0; g4 < n4; ++g4) {
+        float4 w[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            w[r] = reinterpret_cast<const float4 *>(rows + r * gxp)[g4];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float dx[4];
+            dx[0] = fmaf(qf, mh, kxp[t]);
+            dx[1] = dx[0] - h;
+            dx[2] = dx[0] - h2;
+            dx[3] = dx[0] - h3;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float rho = j == 0 ? w[r].x : j == 1 ? w[r].y : j == 2 ? w[r].z : w[r].w;
+                    const float r2 = fmaf(dx[j], dx[j], s2[r][t]);
+                    const float wt = rho * rsqrt_sfu(r2);
+                    if (ENERGY) {
+                        sw[r][t] = fmaf(wt, r2, sw[r][t]);     // rho * |d|
+                    } else {
+                        sw[r][t] += wt;
+                        sx[t] = fmaf(wt, dx[j], sx[t]);
+                    }
+                }
+            }
+        }
+        qf += 4.f;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (ENERGY) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) st[t][0] += sw[r][t];
+        } else {
+            st[t][0] += sx[t];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                st[t][1] = fmaf(ky[t] - yr[r], sw[r][t], st[t][1]);
+                st[t][2] = fmaf(kz[t] - zr[r], sw[r][t], st[t][2]);
+            }
+        }
     }
 }
 
-template <class Acc, bool ENERGY>
+template <int ACC, bool ENERGY>
 __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, int64_t r1,
-                                   int slot, const float *xs, float *stage, uint64_t *bars,
+                                   int slot, float *stage, uint64_t *bars, void *accbase,
                                    uint32_t &consumed)
 {
     constexpr int T = kTargetsPerThread;
+    constexpr int NV = ENERGY ? 1 : 3;
     const int tid = threadIdx.x;
-    float kx[T], ky[T], kz[T];
+    float kxp[T], ky[T], kz[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int64_t i = tile * kTile + t * kThreads + tid;
         const float4 p = i < a.N ? a.tgt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        kx[t] = p.x; ky[t] = p.y; kz[t] = p.z;
+        kxp[t] = (float)((double)p.x - a.x0);
+        ky[t] = p.y;
+        kz[t] = p.z;
     }
-    Acc ax[T], ay[T], az[T];
+    SmemAcc<ACC> acc(accbase, tid);
+    acc.zero(T * NV);
     const int R = a.rows_per_stage;
     const uint32_t nst = (uint32_t)((r1 - r0 + R - 1) / R);
     const int gxp = a.gxp;
@@ -137,8 +236,6 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
         for (uint32_t s = 0; s < nst && s < (uint32_t)kStages; ++s)
             issue(s);
 
-    const float4 *xs4 = reinterpret_cast<const float4 *>(xs);
-    const int n4 = gxp >> 2;
     const float *ys = a.coords + gxp;
     const float *zs = ys + a.ny;
     for (uint32_t s = 0; s < nst; ++s) {
@@ -154,42 +251,26 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
         const int64_t rs = r0 + (int64_t)s * R;
         const int nrows = (int)((rs + R < r1 ? rs + R : r1) - rs);
         int iy = (int)(rs % a.ny), iz = (int)(rs / a.ny);
-        for (int rr = 0; rr < nrows; ++rr) {
-            const float yq = ys[iy], zq = zs[iz];
+        float st[T][3];
+#pragma unroll
+        for (int t = 0; t < T; ++t) st[t][0] = st[t][1] = st[t][2] = 0.f;
+        int rr = 0;
+        for (; rr + 1 < nrows; rr += 2) {
+            float yr[2], zr[2];
+            yr[0] = ys[iy]; zr[0] = zs[iz];
             if (++iy == a.ny) { iy = 0; ++iz; }
-            float dy[T], dz[T], s2[T], sw[T], sx[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                dy[t] = ky[t] - yq;
-                dz[t] = kz[t] - zq;
-                s2[t] = fmaf(dy[t], dy[t], fmaf(dz[t], dz[t], kEps2));
-                sw[t] = 0.f;
-                sx[t] = 0.f;
-            }
-            const float4 *row = reinterpret_cast<const float4 *>(buf + rr * gxp);
-#pragma unroll 2
-            for (int g4 = 0; g4 < n4; ++g4) {
-                const float4 w4 = row[g4];
-                const float4 x4 = xs4[g4];
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    attr_pair<ENERGY>(kx[t], s2[t], x4.x, w4.x, sw[t], sx[t]);
-                    attr_pair<ENERGY>(kx[t], s2[t], x4.y, w4.y, sw[t], sx[t]);
-                    attr_pair<ENERGY>(kx[t], s2[t], x4.z, w4.z, sw[t], sx[t]);
-                    attr_pair<ENERGY>(kx[t], s2[t], x4.w, w4.w, sw[t], sx[t]);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                if (ENERGY) {
-                    ax[t].add(sw[t]);
-                } else {
-                    ax[t].add(sx[t]);
-                    ay[t].add(dy[t] * sw[t]);
-                    az[t].add(dz[t] * sw[t]);
-                }
-            }
+            yr[1] = ys[iy]; zr[1] = zs[iz];
+            if (++iy == a.ny) { iy = 0; ++iz; }
+            attr_rows<ENERGY, 2>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
         }
+        if (rr < nrows) {
+            float yr[1] = {ys[iy]}, zr[1] = {zs[iz]};
+            attr_rows<ENERGY, 1>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc.add(t * NV + v, st[t][v]);
         __syncthreads();   // every thread is done with this buffer
         if (tid == 0 && s + kStages < nst) {
             fence_proxy_async_smem();
@@ -201,23 +282,22 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
     for (int t = 0; t < T; ++t) {
         const int l = t * kThreads + tid;
         if (tile * kTile + l < a.N) {
-            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, ax[t].value())
-                               : make_dacc4(ax[t].value(), ay[t].value(), az[t].value(), 0.0);
+            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, acc.value(t))
+                             : make_dacc4(acc.value(3 * t), acc.value(3 * t + 1),
+                                          acc.value(3 * t + 2), 0.0);
             a.part[(tile * a.sp.slots + slot) * kTile + l] = v;
         }
     }
     return true;
 }
 
-template <class Acc, bool ENERGY>
-__global__ void __launch_bounds__(kThreads) attraction_kernel(const AttrArgs a)
+template <int ACC, bool ENERGY>
+__global__ void __launch_bounds__(kThreads, 3) attraction_kernel(const AttrArgs a)
 {
     extern __shared__ __align__(128) float smem[];
-    float *xs = smem;                                   // gxp floats (gxp % 4 == 0)
-    float *stage = smem + a.gxp;                        // kStages * kStageFloats
+    void *accbase = smem;                                     // kAccBytes
+    float *stage = smem + kAccBytes / sizeof(float);          // kStages * kStageFloats
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStages * kStageFloats);
-    for (int q = threadIdx.x; q < a.gxp; q += kThreads)
-        xs[q] = a.coords[q];
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s)
             mbar_init(&bars[s], 1);
@@ -233,7 +313,8 @@ __global__ void __launch_bounds__(kThreads) attraction_kernel(const AttrArgs a)
         const int64_t r0 = u - tile * rows;
         const int64_t r1 = rows < r0 + (uend - u) ? rows : r0 + (uend - u);
         const int slot = (int)(blockIdx.x - split_cta_of(a.sp, tile * rows));
-        if (!attraction_segment<Acc, ENERGY>(a, tile, r0, r1, slot, xs, stage, bars, consumed))
+        if (!attraction_segment<ACC, ENERGY>(a, tile, r0, r1, slot, stage, bars, accbase,
+                                             consumed))
             return;
         u += r1 - r0;
     }
@@ -255,11 +336,13 @@ __device__ __forceinline__ void rep_pair(float kx, float ky, float kz, const flo
     }
 }
 
-template <class Acc, bool ENERGY>
+template <int ACC, bool ENERGY>
 __device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, int64_t b1, int slot,
-                                  float4 *stage, uint64_t *bars, uint32_t &consumed)
+                                  float4 *stage, uint64_t *bars, void *accbase,
+                                  uint32_t &consumed)
 {
     constexpr int T = kTargetsPerThread;
+    constexpr int NV = ENERGY ? 1 : 3;
     const int tid = threadIdx.x;
     float kx[T], ky[T], kz[T];
 #pragma unroll
@@ -268,7 +351,8 @@ __device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, in
         const float4 p = i < a.N ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         kx[t] = p.x; ky[t] = p.y; kz[t] = p.z;
     }
-    Acc ax[T], ay[T], az[T];
+    SmemAcc<ACC> acc(accbase, tid);
+    acc.zero(T * NV);
     const uint32_t nst = (uint32_t)(b1 - b0);
     auto count_of = [&](int64_t b) -> int {
         const int64_t rem = a.N - b * kSrcBlock;
@@ -298,7 +382,7 @@ __device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, in
 #pragma unroll
         for (int t = 0; t < T; ++t) { rx[t] = 0.f; ry[t] = 0.f; rz[t] = 0.f; }
         if (cnt == kSrcBlock) {
-#pragma unroll 4
+#pragma unroll 2
             for (int j = 0; j < kSrcBlock; ++j) {
                 const float4 q = buf[j];
 #pragma unroll
@@ -315,10 +399,10 @@ __device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, in
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            ax[t].add(rx[t]);
+            acc.add(t * NV, rx[t]);
             if (!ENERGY) {
-                ay[t].add(ry[t]);
-                az[t].add(rz[t]);
+                acc.add(t * NV + 1, ry[t]);
+                acc.add(t * NV + 2, rz[t]);
             }
         }
         __syncthreads();
@@ -332,19 +416,21 @@ __device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, in
     for (int t = 0; t < T; ++t) {
         const int l = t * kThreads + tid;
         if (tile * kTile + l < a.N) {
-            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, ax[t].value())
-                               : make_dacc4(ax[t].value(), ay[t].value(), az[t].value(), 0.0);
+            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, acc.value(t))
+                             : make_dacc4(acc.value(3 * t), acc.value(3 * t + 1),
+                                          acc.value(3 * t + 2), 0.0);
             a.part[(tile * a.sp.slots + slot) * kTile + l] = v;
         }
     }
     return true;
 }
 
-template <class Acc, bool ENERGY>
-__global__ void __launch_bounds__(kThreads) repulsion_kernel(const RepArgs a)
+template <int ACC, bool ENERGY>
+__global__ void __launch_bounds__(kThreads, 3) repulsion_kernel(const RepArgs a)
 {
     extern __shared__ __align__(128) float4 smem4[];
-    float4 *stage = smem4;
+    void *accbase = smem4;
+    float4 *stage = smem4 + kAccBytes / sizeof(float4);
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStages * kSrcBlock);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s)
@@ -361,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) repulsion_kernel(const RepArgs a)
         const int64_t b0 = u - tile * per;
         const int64_t b1 = per < b0 + (uend - u) ? per : b0 + (uend - u);
         const int slot = (int)(blockIdx.x - split_cta_of(a.sp, tile * per));
-        if (!repulsion_segment<Acc, ENERGY>(a, tile, b0, b1, slot, stage, bars, consumed))
+        if (!repulsion_segment<ACC, ENERGY>(a, tile, b0, b1, slot, stage, bars, accbase, consumed))
             return;
         u += b1 - b0;
     }
@@ -465,21 +551,21 @@ cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <class Acc, bool E>
-void *attraction_fn() { return reinterpret_cast<void *>(attraction_kernel<Acc, E>); }
-template <class Acc, bool E>
-void *repulsion_fn() { return reinterpret_cast<void *>(repulsion_kernel<Acc, E>); }
+template <int ACC, bool E>
+void *attraction_fn() { return reinterpret_cast<void *>(attraction_kernel<ACC, E>); }
+template <int ACC, bool E>
+void *repulsion_fn() { return reinterpret_cast<void *>(repulsion_kernel<ACC, E>); }
 
 void *pick_attraction(int acc, bool energy)
 {
-    if (acc == 0) return energy ? attraction_fn<KahanF, true>() : attraction_fn<KahanF, false>();
-    return energy ? attraction_fn<AccD, true>() : attraction_fn<AccD, false>();
+    if (acc == 0) return energy ? attraction_fn<0, true>() : attraction_fn<0, false>();
+    return energy ? attraction_fn<1, true>() : attraction_fn<1, false>();
 }
 
 void *pick_repulsion(int acc, bool energy)
 {
-    if (acc == 0) return energy ? repulsion_fn<KahanF, true>() : repulsion_fn<KahanF, false>();
-    return energy ? repulsion_fn<AccD, true>() : repulsion_fn<AccD, false>();
+    if (acc == 0) return energy ? repulsion_fn<0, true>() : repulsion_fn<0, false>();
+    return energy ? repulsion_fn<1, true>() : repulsion_fn<1, false>();
 }
 
 int grid_for(int64_t n, int threads, int sms)
@@ -512,14 +598,16 @@ cudaError_t launch_pack_grid(const float *rho, int nx, int ny, int nz, int gxp, 
     return cudaGetLastError();
 }
 
-size_t attraction_smem_bytes(int gxp)
+size_t attraction_smem_bytes(int)
 {
-    return ((size_t)gxp + (size_t)kStages * kStageFloats) * sizeof(float) + kStages * sizeof(uint64_t);
+    return (size_t)kAccBytes + (size_t)kStages * kStageFloats * sizeof(float) +
+           kStages * sizeof(uint64_t);
 }
 
 size_t repulsion_smem_bytes()
 {
-    return (size_t)kStages * kSrcBlock * sizeof(float4) + kStages * sizeof(uint64_t);
+    return (size_t)kAccBytes + (size_t)kStages * kSrcBlock * sizeof(float4) +
+           kStages * sizeof(uint64_t);
 }
 
 int attraction_ctas_per_sm(int acc, bool energy, int gxp)
