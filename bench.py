@@ -48,7 +48,11 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hr", "diff", "medium", "small", "tiny"), default="hr")
+    ap.add_argument("--workload", choices=("hr", "diff", "medium", "small", "tiny", "batched"),
+                    default="hr")
+    ap.add_argument("--path", choices=("kernels", "engine"), default="kernels",
+                    help="single-trajectory step through sparkling_step (separate pair kernels) "
+                         "or the persistent engine (sparkling_step_batched with B = 1)")
     ap.add_argument("--acc", choices=("kahan", "fp64"), default="kahan")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -210,8 +214,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    prob = load_problem(args.workload, 0)
-    N, P = prob.N, int(prob.grid.rho.size)
+    if args.workload == "batched":
+        import inputs
+        probs = inputs.make_batched(seed=0)
+        prob = max(probs, key=lambda q: q.N)
+        N = sum(q.N for q in probs)
+        P = int(prob.grid.rho.size)
+        pairs_step = sum(pairs_per_step(q.N, int(q.grid.rho.size)) for q in probs)
+    else:
+        prob = load_problem(args.workload, 0)
+        N, P = prob.N, int(prob.grid.rho.size)
+        pairs_step = pairs_per_step(N, P)
     vals = []
     desc = threads = None
     for _ in range(args.warmup):
@@ -221,7 +234,7 @@ def run_reference(args):
         vals.append(v)
     value = statistics.median(vals)
     unit = "pairs/s"
-    step_s = pairs_per_step(N, P) / value
+    step_s = pairs_step / value
     out = {
         "impl": "reference", "metric": "pair_interactions_per_s", "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -239,6 +252,50 @@ def run_reference(args):
 
 # --- our implementation --------------------------------------------------------
 
+class Workload:
+    """Device state and the step call of one benchmark workload."""
+
+    def __init__(self, sp, args, dev, seed):
+        import torch
+        self.sp, self.args, self.dev = sp, args, dev
+        self.acc = sp.ACC_KAHAN32 if args.acc == "kahan" else sp.ACC_FP64
+        if args.workload == "batched":
+            import inputs
+            self.probs = inputs.make_batched(seed=seed)
+        else:
+            self.probs = [load_problem(args.workload, seed)]
+        self.batched = args.workload == "batched" or args.path == "engine"
+        self.off = [0]
+        for p in self.probs:
+            self.off.append(self.off[-1] + p.N)
+        self.Ns = self.probs[0].Ns
+        self.K = torch.from_numpy(__import__("numpy").concatenate([p.K for p in self.probs])).to(dev)
+        self.rhos = [torch.from_numpy(p.grid.rho).to(dev) for p in self.probs]
+        self.grids = [sp.make_grid(r, p.grid.lo, p.grid.hi, p.grid.n)
+                      for r, p in zip(self.rhos, self.probs)]
+        self.projs = [sp.make_proj(p.proj.alpha, p.proj.beta, p.proj.box, p.proj.n_iter,
+                                   p.proj.pin_index, p.proj.pin) for p in self.probs]
+        self.etas = [p.eta for p in self.probs]
+        self.pairs = sum(pairs_per_step(p.N, int(p.grid.rho.size)) for p in self.probs)
+        self.N = self.off[-1]
+        p0 = self.probs[0]
+        if args.workload == "batched":
+            self.desc = (f"batched: {len(self.probs)} trajectories, N_b = 512 x U{{32..512}} shots "
+                         f"(total {self.N}), 64^3 Gaussian densities")
+        else:
+            self.desc = f"{args.workload}: {p0.recipe}"
+
+    def step(self):
+        sp = self.sp
+        if self.batched:
+            sp.sparkling_step_batched(self.ctx, self.K, self.off, self.Ns, self.grids, self.etas,
+                                      self.projs, self.acc, graph=True)
+        else:
+            p = self.probs[0]
+            sp.sparkling_step(self.ctx, self.K, p.Nc, p.Ns, self.grids[0], p.eta, self.projs[0],
+                              self.acc)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -253,21 +310,14 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2108_02991_gb300 as sp
 
-    prob = load_problem(args.workload, seed=rank)
-    N, P = prob.N, int(prob.grid.rho.size)
-    acc = sp.ACC_KAHAN32 if args.acc == "kahan" else sp.ACC_FP64
-    K0 = torch.from_numpy(prob.K).to(dev)
-    K = K0.clone()
-    rho = torch.from_numpy(prob.grid.rho).to(dev)
-    grid = sp.make_grid(rho, prob.grid.lo, prob.grid.hi, prob.grid.n)
-    pp = prob.proj
-    proj = sp.make_proj(pp.alpha, pp.beta, pp.box, pp.n_iter, pp.pin_index, pp.pin)
+    w = Workload(sp, args, dev, seed=rank)
     ctx = sp.sparkling_create(local)
+    w.ctx = ctx
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
-        sp.sparkling_step(ctx, K, prob.Nc, prob.Ns, grid, prob.eta, proj, acc)
+        w.step()
     sp.sparkling_status(ctx)
     torch.cuda.synchronize(dev)
 
@@ -284,7 +334,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sp.sparkling_step(ctx, K, prob.Nc, prob.Ns, grid, prob.eta, proj, acc)
+        w.step()
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -298,77 +348,101 @@ def run_ours(args):
 
     local_ms = sum(step_ms)
     total_ms = reduce_max(local_ms, dev)
-    pairs_all = reduce_sum(float(pairs_per_step(N, P) * args.steps), dev)
+    pairs_all = reduce_sum(float(w.pairs * args.steps), dev)
     value = pairs_all / (total_ms * 1e-3)
 
-    # dominant kernel: the attraction sum (N*P pairs per launch)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    import json as _json
     peaks = {}
     try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    att_ms, att_n = ktimes["attraction"]
-    rep_ms, rep_n = ktimes["repulsion"]
-    att_pairs = N * P
-    achieved = att_pairs / (att_ms / att_n * 1e-3) if att_n else None
     rsq = measure_rsq_rate() if rank == 0 else None
     rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
     peak = sms * rate * max_mhz * 1e6
+    if w.batched:
+        # one engine launch runs every pair of the step: N_b*P_b + N_b*(N_b-1)
+        kname, kpairs = "engine", w.pairs
+    else:
+        p0 = w.probs[0]
+        kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
+    k_ms, k_n = ktimes[kname]
+    achieved = kpairs / (k_ms / k_n * 1e-3) if k_n else None
     roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak / 1e9, "unit": "Gpair/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "attraction",
+            "kernel": kname,
             "peak_basis": f"{sms} SMs x {rate:g} MUFU.RSQ/clk/SM x {max_mhz:.0f} MHz max SM clock "
                           f"(one reciprocal square root per pair; probe measured "
                           f"{rsq if rsq else 'n/a'} RSQ/clk/SM)"}
     if clk and achieved:
         roof["frac_at_measured_clock"] = achieved / (sms * rate * clk["sm_mhz"] * 1e6)
-    kernels = {k: {"ms_total": round(ms, 3), "launches": n,
-                   "share": round(ms / max(sum(v[0] for v in ktimes.values()), 1e-9), 4)}
-               for k, (ms, n) in ktimes.items()}
-    if rep_n:
-        kernels["repulsion"]["gpair_per_s"] = N * (N - 1) / (rep_ms / rep_n * 1e-3) / 1e9
+    tot_k = max(sum(v[0] for v in ktimes.values()), 1e-9)
+    kernels = {k: {"ms_total": round(ms, 3), "launches": n, "share": round(ms / tot_k, 4)}
+               for k, (ms, n) in ktimes.items() if n}
+    if not w.batched and ktimes["repulsion"][1]:
+        rep_ms, rep_n = ktimes["repulsion"]
+        kernels["repulsion"]["gpair_per_s"] = w.N * (w.N - 1) / (rep_ms / rep_n * 1e-3) / 1e9
 
     e2e = None
-    if not args.no_e2e:
-        Kh = torch.from_numpy(prob.K).pin_memory()
-        rhoh = torch.from_numpy(prob.grid.rho).pin_memory()
-        hgrid = sp.make_grid(rhoh, prob.grid.lo, prob.grid.hi, prob.grid.n)
+    if not args.no_e2e and not w.batched:
+        p = w.probs[0]
+        Kh = torch.from_numpy(p.K).pin_memory()
+        rhoh = torch.from_numpy(p.grid.rho).pin_memory()
+        hgrid = sp.make_grid(rhoh, p.grid.lo, p.grid.hi, p.grid.n)
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            sp.sparkling_step_host(ctx, Kh, prob.Nc, prob.Ns, hgrid, rhoh, prob.eta, proj, acc)
+            sp.sparkling_step_host(ctx, Kh, p.Nc, p.Ns, hgrid, rhoh, p.eta, w.projs[0], w.acc)
         t1 = time.perf_counter()
         barrier()
         e2e_s = reduce_max(t1 - t0, dev)
         e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s",
                "h2d_bytes_per_step": int(Kh.numel() * Kh.element_size() + rhoh.numel() * 4),
                "d2h_bytes_per_step": int(Kh.numel() * Kh.element_size())}
+    elif not args.no_e2e:
+        # batched: pinned host copy of K in and out around every step
+        Kh = w.K.cpu().pin_memory()
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            w.K.copy_(Kh, non_blocking=True)
+            w.step()
+            Kh.copy_(w.K, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = reduce_max(t1 - t0, dev)
+        nb = int(Kh.numel() * Kh.element_size())
+        e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "note": "densities resident on the device"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, threads = oracle_sample(prob, args.cpu_seconds)
+        v, desc, threads = oracle_sample(w.probs[0], args.cpu_seconds)
         cpu = {"value": v, "unit": "pairs/s", "cores": threads, "kind": "oracle", "sample": desc}
 
     if rank == 0:
+        p0 = w.probs[0]
         out = {
             "metric": "pair_interactions_per_s", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 pairs, " + ("compensated-f32" if acc == 0 else "f64")
-            + " per-target sums, f64 projection",
+            "vs_baseline": None,
+            "dtype": "f32 pairs, " + ("compensated-f32" if w.acc == 0 else "f64")
+                     + " per-target sums, f64 projection",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {prob.recipe}", "N": N, "P": P,
-                       "Nc": prob.Nc, "Ns": prob.Ns, "pairs_per_step": pairs_per_step(N, P),
-                       "n_pit": pp.n_iter, "l2": "flushed (512 MB write) between timed steps",
-                       "acc": args.acc},
+            "config": {"workload": w.desc, "N": w.N, "P": int(p0.grid.rho.size),
+                       "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
+                       "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
+                       "l2": "flushed (512 MB write) between timed steps", "acc": args.acc},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,
+            "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
         }
         print(json.dumps(out), flush=True)
     ctx.close()

@@ -117,7 +117,11 @@ typedef struct sparkling_proj {
 #define SPARKLING_KERNEL_REPULSION 2
 #define SPARKLING_KERNEL_COMBINE 3
 #define SPARKLING_KERNEL_PROJECT 4
-#define SPARKLING_KERNEL_COUNT 5
+#define SPARKLING_KERNEL_ENGINE 5   /* a whole batched step (packs + persistent engine) */
+#define SPARKLING_KERNEL_COUNT 6
+
+/* Flags of sparkling_step_batched. */
+#define SPARKLING_BATCH_GRAPH 1     /* replay the step from a cached CUDA graph */
 
 /* Create a context bound to CUDA device `device`.  Nothing is allocated on
  * the device and no CUDA call is made until the first compute call.
@@ -187,6 +191,34 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
                                  const sparkling_grid *grid, int acc, double eta,
                                  const sparkling_proj *proj, void *stream);
 
+/* One projected-gradient step K_b <- Pi(K_b - eta_b G(K_b)) for B
+ * independent trajectories of uneven size in ONE persistent kernel launch
+ * (plus the packing of samples and densities): a work list of attraction
+ * items (a tile of 1024 targets against a run of grid rows) and repulsion
+ * items (against a run of source blocks), interleaved so that each SM mixes
+ * SFU-bound and issue-bound work, followed by one projection item per shot
+ * that waits (bounded) for its trajectory's pair items.  Same arithmetic as
+ * sparkling_step: FP32 pairs, acc per-target folds, FP64 gradient, step and
+ * projection (fixed n_iter; converged mode is not available here).
+ *   traj_off  host [B+1]: trajectory b is samples [traj_off[b], traj_off[b+1])
+ *             of K; traj_off[0] = 0; every trajectory holds >= 2 samples and
+ *             a whole number of shots of Ns samples
+ *   K         device [traj_off[B]][3] of K_dtype, updated in place
+ *   grids     host [B] density grids (rho on the device); eta host [B];
+ *   proj      host [B] constraint sets (tol must be <= 0)
+ *   flags     SPARKLING_BATCH_GRAPH: from the second call with the same
+ *             shapes, K, densities and workspace on, the device work of the
+ *             step is captured once into a CUDA graph and replayed (calls on
+ *             a stream the caller is itself capturing are never captured).
+ * The work list is planned and uploaded when the shapes change; make the
+ * first call of a shape outside any caller-side stream capture.  The item
+ * granularity comes from the context's autotuned setting.  Asynchronous. */
+SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const int64_t *traj_off,
+                                         void *K, int K_dtype, int32_t Ns,
+                                         const sparkling_grid *grids, const double *eta,
+                                         const sparkling_proj *proj, int acc, int flags,
+                                         void *stream);
+
 /* sparkling_step on HOST buffers: K_host [Nc*Ns][3] (K_dtype) is copied to
  * the device, stepped, and copied back; rho_host [nz][ny][nx] float32 is
  * copied to the device (grid->rho is ignored).  Blocks until K_host holds
@@ -229,11 +261,30 @@ SPARKLING_API int sparkling_status(sparkling_ctx *ctx, void *stream);
 /* Kernel timing: when enabled, every kernel launch of the context is
  * bracketed by CUDA events on its stream.  sparkling_kernel_times()
  * synchronises the pending events and writes, for the first n kinds
- * (SPARKLING_KERNEL_*), the total milliseconds and the number of launches
- * since the last reset; reset != 0 clears the totals afterwards. */
+ * (SPARKLING_KERNEL_*), the total milliseconds and the number of timed
+ * scopes since the last reset (one per launch, except PACK -- samples and
+ * density packed together -- COMBINE in energy mode -- two reduction kernels
+ * -- and ENGINE -- a whole batched step); reset != 0 clears the totals
+ * afterwards. */
 SPARKLING_API int sparkling_set_timing(sparkling_ctx *ctx, int enable);
 SPARKLING_API int sparkling_kernel_times(sparkling_ctx *ctx, double *ms_out, int64_t *launches_out,
                                          int n, int reset);
+
+/* Autotuner of the tile shapes of the pair kernels (threads per CTA, i.e.
+ * targets held in registers per thread, and the unroll of the repulsion's
+ * source loop).  When enabled (the default), the first sparkling_grad /
+ * sparkling_energy / sparkling_step call of a new key -- accumulation mode and
+ * padded grid-row length for the attraction, accumulation mode for the
+ * repulsion -- times every shape on a prefix of the caller's own problem
+ * (about 1e11 pairs each; this synchronises the stream) and keeps the fastest
+ * for the context.  enable = 0 uses the default shapes for keys not tuned yet,
+ * 1 tunes, -1 forgets every choice and tunes again.  Nothing is tuned on a
+ * stream that is being captured. */
+SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
+
+/* Text of the tuning trials (pairs/s per shape) and of the choices, NUL
+ * terminated, truncated to len bytes. */
+SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len);
 
 /* Number of kernels this context has launched since it was created. */
 SPARKLING_API int64_t sparkling_launch_count(const sparkling_ctx *ctx);

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libsparkling.so")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV = range(7)
 F32, F64 = 0, 1
 ACC_KAHAN32, ACC_FP64 = 0, 1
-KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project")
+KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine")
+BATCH_GRAPH = 1
 
 # Every entry point declared in include/sparkling.h.
 ABI_SYMBOLS = (
@@ -26,6 +27,7 @@ ABI_SYMBOLS = (
     "sparkling_energy", "sparkling_energy_backward", "sparkling_project", "sparkling_step",
     "sparkling_step_host", "sparkling_status", "sparkling_set_timing", "sparkling_kernel_times",
     "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
+    "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
 )
 
 
@@ -80,6 +82,10 @@ def lib() -> ctypes.CDLL:
             "sparkling_launch_count": ([p], i64),
             "sparkling_version": ([], ctypes.c_char_p),
             "sparkling_grad_noalloc": ([p, i, i64, ctypes.POINTER(Grid), i, p, i, p], i),
+            "sparkling_set_autotune": ([p, i], i),
+            "sparkling_tuning_report": ([p, p, i64], i),
+            "sparkling_step_batched": ([p, ctypes.c_int32, p, p, i, ctypes.c_int32,
+                                        ctypes.POINTER(Grid), p, ctypes.POINTER(Proj), i, i, p], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -266,6 +272,23 @@ def sparkling_step(ctx: Context, K, Nc: int, Ns: int, grid: Grid, eta: float, pr
                                      ctypes.byref(proj), _stream(stream)))
 
 
+def sparkling_step_batched(ctx: Context, K, traj_off: Sequence[int], Ns: int,
+                           grids: Sequence[Grid], etas: Sequence[float], projs: Sequence[Proj],
+                           acc: int = ACC_KAHAN32, graph: bool = True, stream=None):
+    """One projected-gradient step of B trajectories (samples
+    [traj_off[b], traj_off[b+1]) of K) in one persistent launch, in place."""
+    B = len(grids)
+    if len(traj_off) != B + 1 or len(etas) != B or len(projs) != B:
+        raise ValueError("traj_off needs B+1 entries, etas and projs B")
+    off = (ctypes.c_int64 * (B + 1))(*[int(v) for v in traj_off])
+    garr = (Grid * B)(*grids)
+    earr = (ctypes.c_double * B)(*[float(v) for v in etas])
+    parr = (Proj * B)(*projs)
+    _check(ctx, lib().sparkling_step_batched(ctx.handle, B, off, _dev_ptr(K, "K"), _dtype_code(K),
+                                             int(Ns), garr, earr, parr, acc,
+                                             BATCH_GRAPH if graph else 0, _stream(stream)))
+
+
 def sparkling_step_host(ctx: Context, K_host, Nc: int, Ns: int, grid: Grid, rho_host, eta: float,
                         proj: Proj, acc: int = ACC_KAHAN32, stream=None):
     """sparkling_step on host tensors (CPU, contiguous; pinned for async DMA)."""
@@ -296,6 +319,17 @@ def sparkling_kernel_times(ctx: Context, reset: bool = False):
     cnt = (ctypes.c_int64 * n)()
     _check(ctx, lib().sparkling_kernel_times(ctx.handle, ms, cnt, n, 1 if reset else 0))
     return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def sparkling_set_autotune(ctx: Context, enable: int = 1) -> None:
+    """1: tune tile shapes at first use (default); 0: default shapes; -1: retune."""
+    _check(ctx, lib().sparkling_set_autotune(ctx.handle, int(enable)))
+
+
+def sparkling_tuning_report(ctx: Context) -> str:
+    buf = ctypes.create_string_buffer(8192)
+    _check(ctx, lib().sparkling_tuning_report(ctx.handle, buf, len(buf)))
+    return buf.value.decode()
 
 
 def sparkling_launch_count(ctx: Context) -> int:

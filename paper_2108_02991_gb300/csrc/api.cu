@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,10 +41,37 @@ struct sparkling_ctx {
     double ms[SPARKLING_KERNEL_COUNT] = {};
     int64_t nlaunch[SPARKLING_KERNEL_COUNT] = {};
     int64_t launches = 0;
-    // occupancy cache
-    int occ_attr[2][2] = {{-1, -1}, {-1, -1}};
-    int occ_attr_gxp[2][2] = {{-1, -1}, {-1, -1}};
-    int occ_rep[2][2] = {{-1, -1}, {-1, -1}};
+    // occupancy cache [acc][energy][variant]
+    int occ_attr[2][2][kAttrVariants] = {};
+    int occ_rep[2][2][kRepVariants] = {};
+    bool occ_done = false;
+    // autotuner: tile shape per (acc, padded row length) for the attraction
+    // and per acc for the repulsion; -1 = not tuned yet
+    bool autotune = true;
+    std::vector<std::pair<int64_t, int>> attr_choice;   // key acc * 2^20 + gxp
+    int rep_choice[2] = {-1, -1};
+    std::string tune_log;
+    // batched step: cached work list, workspace layout and CUDA graph
+    struct Batch {
+        bool valid = false;
+        int B = 0, Ns = 0, acc = -1, dtype = -1, ctas = 0, items_per_cta = 0;
+        std::vector<int64_t> off;
+        std::vector<int32_t> dims;
+        std::vector<EngineTraj> traj;
+        std::vector<EngineItem> items;
+        std::vector<size_t> o_rho, o_coords;
+        size_t o_pos = 0, o_traj = 0, o_items = 0, o_cnt = 0, o_part = 0, o_gstate = 0, end = 0;
+        bool proj_in_smem = false;
+        int64_t kernels_per_step = 0;
+        // graph of the device work of one step (counters, packs, engine)
+        cudaGraphExec_t exec = nullptr;
+        std::vector<const void *> graph_key;
+        int eager_calls = 0;
+    } batch;
+    cudaStream_t cap_stream = nullptr;  // private stream the batched step is captured on
+    EngineTraj *h_traj = nullptr;   // pinned staging of the trajectory descriptors
+    size_t h_traj_cap = 0;
+    int items_per_cta = 16;         // work-list granularity (autotuned)
 };
 
 namespace {
@@ -165,10 +193,12 @@ struct LaunchScope {
             if (a) cudaEventRecord(a, st);
         }
     }
+    // nkernels: kernels launched inside the scope (all counted in
+    // sparkling_launch_count); the timing table counts the scope once.
     void done(int nkernels = 1)
     {
         ctx->launches += nkernels;
-        ctx->nlaunch[kind] += nkernels;
+        ctx->nlaunch[kind] += 1;
         if (a && b) {
             cudaEventRecord(b, st);
             ctx->pending.push_back({kind, a, b});
@@ -227,36 +257,78 @@ struct PairPlan {
     int64_t N;
     int nx, ny, nz, gxp;
     int64_t tiles;
+    int va, vr;            // tile shapes (autotuner variants) of the two pair kernels
     Split spa, spr;
     size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_eblocks, o_g64, end;
 };
 
+int ensure_occupancy(sparkling_ctx *ctx)
+{
+    if (ctx->occ_done) return SPARKLING_OK;
+    for (int acc = 0; acc < 2; ++acc)
+        for (int e = 0; e < 2; ++e) {
+            for (int v = 0; v < kAttrVariants; ++v)
+                ctx->occ_attr[acc][e][v] = attraction_ctas_per_sm(acc, e != 0, v);
+            for (int v = 0; v < kRepVariants; ++v)
+                ctx->occ_rep[acc][e][v] = repulsion_ctas_per_sm(acc, e != 0, v);
+        }
+    cudaGetLastError();
+    for (int acc = 0; acc < 2; ++acc)
+        for (int e = 0; e < 2; ++e)
+            if (ctx->occ_attr[acc][e][kAttrDefault] < 1 || ctx->occ_rep[acc][e][kRepDefault] < 1)
+                return fail(ctx, SPARKLING_E_CUDA, "pair kernels cannot be resident (occupancy 0)");
+    ctx->occ_done = true;
+    return SPARKLING_OK;
+}
+
+int attr_choice_of(const sparkling_ctx *ctx, int acc, int gxp)
+{
+    const int64_t key = (int64_t)acc * (1 << 20) + gxp;
+    for (const auto &kv : ctx->attr_choice)
+        if (kv.first == key) return kv.second;
+    return -1;
+}
+
+// Splits of the two pair kernels for the chosen tile shapes.
+void set_splits(sparkling_ctx *ctx, PairPlan &P, int acc, bool energy, int va, int vr)
+{
+    const int e = energy ? 1 : 0;
+    const int64_t rows = (int64_t)P.ny * P.nz;
+    const int64_t nblocks = (P.N + kSrcBlock - 1) / kSrcBlock;
+    P.va = va;
+    P.vr = vr;
+    P.spa = make_split(P.tiles, rows, (int64_t)ctx->sms * ctx->occ_attr[acc][e][va]);
+    P.spr = make_split(P.tiles, nblocks, (int64_t)ctx->sms * ctx->occ_rep[acc][e][vr]);
+}
+
 int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, bool energy,
                bool need_g64, PairPlan &P, Carve &cv)
 {
+    int s;
+    if ((s = ensure_occupancy(ctx))) return s;
     P.N = N;
     P.nx = g->n[0]; P.ny = g->n[1]; P.nz = g->n[2];
     P.gxp = (P.nx + 3) / 4 * 4;
     P.tiles = (N + kTile - 1) / kTile;
-    const int e = energy ? 1 : 0;
-    if (ctx->occ_attr[acc][e] < 0 || ctx->occ_attr_gxp[acc][e] != P.gxp) {
-        ctx->occ_attr[acc][e] = attraction_ctas_per_sm(acc, energy, P.gxp);
-        ctx->occ_attr_gxp[acc][e] = P.gxp;
+    const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[acc];
+    set_splits(ctx, P, acc, energy, va < 0 ? kAttrDefault : va, vr < 0 ? kRepDefault : vr);
+    // Partial buffers big enough for every tile shape and for the tuning
+    // trials (which run on a prefix of the tiles with one wave of CTAs).
+    int64_t max_ctas = 0;
+    for (int e = 0; e < 2; ++e) {
+        for (int v = 0; v < kAttrVariants; ++v)
+            max_ctas = std::max<int64_t>(max_ctas, (int64_t)ctx->sms * ctx->occ_attr[acc][e][v]);
+        for (int v = 0; v < kRepVariants; ++v)
+            max_ctas = std::max<int64_t>(max_ctas, (int64_t)ctx->sms * ctx->occ_rep[acc][e][v]);
     }
-    if (ctx->occ_rep[acc][e] < 0) ctx->occ_rep[acc][e] = repulsion_ctas_per_sm(acc, energy);
-    if (ctx->occ_attr[acc][e] < 1 || ctx->occ_rep[acc][e] < 1) {
-        cudaGetLastError();
-        return fail(ctx, SPARKLING_E_CUDA, "pair kernels cannot be resident (occupancy 0)");
-    }
+    const int64_t part_units = std::max<int64_t>(P.tiles * ((max_ctas + P.tiles - 1) / P.tiles + 1),
+                                                 max_ctas + 2 * P.tiles);
     const int64_t rows = (int64_t)P.ny * P.nz;
-    const int64_t nblocks = (N + kSrcBlock - 1) / kSrcBlock;
-    P.spa = make_split(P.tiles, rows, (int64_t)ctx->sms * ctx->occ_attr[acc][e]);
-    P.spr = make_split(P.tiles, nblocks, (int64_t)ctx->sms * ctx->occ_rep[acc][e]);
     P.o_pos = cv.take((size_t)N * sizeof(float4));
     P.o_rho = cv.take((size_t)rows * P.gxp * sizeof(float));
     P.o_coords = cv.take(((size_t)P.gxp + P.ny + P.nz) * sizeof(float));
-    P.o_parta = cv.take((size_t)P.tiles * P.spa.slots * kTile * sizeof(dacc4));
-    P.o_partr = cv.take((size_t)P.tiles * P.spr.slots * kTile * sizeof(dacc4));
+    P.o_parta = cv.take((size_t)part_units * kTile * sizeof(dacc4));
+    P.o_partr = cv.take((size_t)part_units * kTile * sizeof(dacc4));
     P.o_eblocks = cv.take((size_t)energy_blocks(N) * sizeof(double2));
     P.o_g64 = need_g64 ? cv.take((size_t)N * 3 * sizeof(double)) : 0;
     P.end = cv.off;
@@ -268,9 +340,81 @@ template <typename T> T *at(sparkling_ctx *ctx, size_t off)
     return reinterpret_cast<T *>(static_cast<char *>(ctx->ws) + off);
 }
 
-// pack -> attraction -> repulsion -> combine (gradient) or energy reduction.
+// Autotuner: time every tile shape of a pair kernel on a prefix of the
+// caller's own (already packed) problem -- about 1e11 pairs, one wave of
+// CTAs, one warm-up and one timed launch each -- and keep the fastest.  The
+// trials write into the partial buffers, which the real launch overwrites.
+// Runs once per key (acc and padded row length for the attraction, acc for
+// the repulsion) and synchronises the stream.
+int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra, bool do_attr,
+               bool do_rep, cudaStream_t st)
+{
+    cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+    const int64_t rows = (int64_t)P.ny * P.nz;
+    const int64_t nblocks = (P.N + kSrcBlock - 1) / kSrcBlock;
+    const double budget = 1e11;
+    char line[160];
+    auto timed = [&](auto launch) -> double {
+        cudaError_t err = launch();
+        if (err != cudaSuccess) return -1.0;
+        cudaEventRecord(e0, st);
+        err = launch();
+        cudaEventRecord(e1, st);
+        if (err != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    if (do_attr) {
+        const int64_t P3 = rows * P.nx;
+        int64_t tt = (int64_t)(budget / ((double)kTile * (double)P3) + 0.5);
+        tt = std::max<int64_t>(1, std::min<int64_t>(tt, P.tiles));
+        int best = kAttrDefault;
+        double best_rate = 0.0;
+        for (int v = 0; v < kAttrVariants; ++v) {
+            const int occ = ctx->occ_attr[acc][0][v];
+            if (occ < 1) continue;
+            aa.sp = make_split(tt, rows, (int64_t)ctx->sms * occ);
+            const double ms = timed([&] { return launch_attraction(aa, acc, false, v, st); });
+            const double pairs = (double)std::min<int64_t>(tt * kTile, P.N) * (double)P3;
+            const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
+            snprintf(line, sizeof line, "attraction gxp=%d threads=%d: %.4g pairs/s\n", P.gxp,
+                     attr_variant_threads(v), rate);
+            ctx->tune_log += line;
+            if (rate > best_rate) { best_rate = rate; best = v; }
+        }
+        ctx->attr_choice.push_back({(int64_t)acc * (1 << 20) + P.gxp, best});
+    }
+    if (do_rep) {
+        int64_t tt = (int64_t)(budget / ((double)kTile * (double)P.N) + 0.5);
+        tt = std::max<int64_t>(1, std::min<int64_t>(tt, P.tiles));
+        int best = kRepDefault;
+        double best_rate = 0.0;
+        for (int v = 0; v < kRepVariants; ++v) {
+            const int occ = ctx->occ_rep[acc][0][v];
+            if (occ < 1) continue;
+            ra.sp = make_split(tt, nblocks, (int64_t)ctx->sms * occ);
+            const double ms = timed([&] { return launch_repulsion(ra, acc, false, v, st); });
+            const double pairs = (double)std::min<int64_t>(tt * kTile, P.N) * (double)P.N;
+            const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
+            snprintf(line, sizeof line, "repulsion threads=%d unroll=%d: %.4g pairs/s\n",
+                     rep_variant_threads(v), rep_variant_unroll(v), rate);
+            ctx->tune_log += line;
+            if (rate > best_rate) { best_rate = rate; best = v; }
+        }
+        ctx->rep_choice[acc] = best;
+    }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "autotuner trial");
+    return SPARKLING_OK;
+}
+
+// pack -> (autotune) -> attraction -> repulsion -> combine (gradient) or
+// energy reduction.
 int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_grid *g, int acc,
-              bool energy, const PairPlan &P, void *G, int G_dtype, void *A, void *R, bool g64,
+              bool energy, PairPlan &P, void *G, int G_dtype, void *A, void *R, bool g64,
               cudaStream_t st, double scale = 1.0, const double *scale_dev = nullptr)
 {
     float4 *pos = at<float4>(ctx, P.o_pos);
@@ -289,18 +433,31 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     aa.rows_per_stage = kStageFloats / P.gxp;
     aa.hx = (float)((g->hi - g->lo) / P.nx);
     aa.x0 = g->lo + 0.5 * ((g->hi - g->lo) / P.nx);
-    aa.sp = P.spa; aa.part = at<dacc4>(ctx, P.o_parta); aa.status = ctx->d_status;
+    aa.part = at<dacc4>(ctx, P.o_parta); aa.status = ctx->d_status;
+    RepArgs ra;
+    ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
+    ra.status = ctx->d_status;
+    const bool need_a = attr_choice_of(ctx, acc, P.gxp) < 0, need_r = ctx->rep_choice[acc] < 0;
+    if (ctx->autotune && (need_a || need_r)) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cap));
+        if (cap == cudaStreamCaptureStatusNone) {
+            int s = tune_pairs(ctx, P, acc, aa, ra, need_a, need_r, st);
+            if (s) return s;
+            const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[acc];
+            set_splits(ctx, P, acc, energy, va < 0 ? kAttrDefault : va, vr < 0 ? kRepDefault : vr);
+        }
+    }
+    aa.sp = P.spa;
+    ra.sp = P.spr;
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_ATTRACTION, st);
-        CK(launch_attraction(aa, acc, energy, st));
+        CK(launch_attraction(aa, acc, energy, P.va, st));
         ls.done();
     }
-    RepArgs ra;
-    ra.pos = pos; ra.N = P.N; ra.sp = P.spr; ra.part = at<dacc4>(ctx, P.o_partr);
-    ra.status = ctx->d_status;
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
-        CK(launch_repulsion(ra, acc, energy, st));
+        CK(launch_repulsion(ra, acc, energy, P.vr, st));
         ls.done();
     }
     CombineArgs cb;
@@ -429,6 +586,147 @@ int check_shots(sparkling_ctx *ctx, int64_t Nc, int64_t Ns)
 
 } // namespace
 
+// ---------------------------------------------------------------------------
+// Batched step on the persistent engine.
+
+namespace {
+
+int64_t pair_cost(int64_t N, int64_t P) { return N * P + N * N; }
+
+// Work list of one batched step: per trajectory and target tile, attraction
+// items (runs of grid rows) and repulsion items (runs of source blocks), each
+// of about total / (ctas * items_per_cta) pairs, then one projection item per
+// shot.  Attraction and repulsion items alternate so that neighbouring CTAs
+// (and hence the CTAs resident on one SM) mix SFU-bound and issue-bound work.
+void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
+                     const sparkling_grid *grids, int ctas, int items_per_cta)
+{
+    const int B = (int)off.size() - 1;
+    int64_t total = 0;
+    for (int t = 0; t < B; ++t) {
+        const int64_t P = (int64_t)grids[t].n[0] * grids[t].n[1] * grids[t].n[2];
+        total += pair_cost(off[t + 1] - off[t], P);
+    }
+    const double target = (double)total / ((double)ctas * items_per_cta);
+    b.traj.assign(B, EngineTraj());
+    b.items.clear();
+    int64_t part = 0;
+    for (int t = 0; t < B; ++t) {
+        EngineTraj &tr = b.traj[t];
+        const int64_t N = off[t + 1] - off[t];
+        const int nx = grids[t].n[0], ny = grids[t].n[1], nz = grids[t].n[2];
+        const int gxp = (nx + 3) / 4 * 4;
+        const int64_t rows = (int64_t)ny * nz;
+        const int64_t blocks = (N + kSrcBlock - 1) / kSrcBlock;
+        int64_t rc = (int64_t)(target / ((double)kTile * gxp) + 0.5);
+        rc = rc < 1 ? 1 : (rc > rows ? rows : rc);
+        int64_t sc = (int64_t)(target / ((double)kTile * kSrcBlock) + 0.5);
+        sc = sc < 1 ? 1 : (sc > blocks ? blocks : sc);
+        const int ach = (int)((rows + rc - 1) / rc), rch = (int)((blocks + sc - 1) / sc);
+        tr.off = off[t];
+        tr.N = N;
+        tr.Ns = b.Ns;
+        tr.Nc = (int32_t)(N / b.Ns);
+        tr.gxp = gxp; tr.ny = ny; tr.nz = nz;
+        tr.rows_per_stage = kStageFloats / gxp;
+        tr.tiles = (int32_t)((N + kTile - 1) / kTile);
+        tr.a_chunks = ach;
+        tr.slots = ach + rch;
+        tr.part_off = part * kTile;
+        part += (int64_t)tr.tiles * tr.slots;
+        tr.n_pair_items = tr.tiles * tr.slots;
+        for (int64_t tile = 0; tile < tr.tiles; ++tile) {
+            int ia = 0, ir = 0;
+            while (ia < ach || ir < rch) {
+                if (ia < ach) {
+                    EngineItem it;
+                    it.kind = kItemAttraction; it.traj = t; it.tile = (int32_t)tile; it.slot = ia;
+                    it.u0 = ia * rc;
+                    it.u1 = (ia + 1) * rc < rows ? (ia + 1) * rc : rows;
+                    b.items.push_back(it);
+                    ++ia;
+                }
+                if (ir < rch) {
+                    EngineItem it;
+                    it.kind = kItemRepulsion; it.traj = t; it.tile = (int32_t)tile;
+                    it.slot = ach + ir;
+                    it.u0 = ir * sc;
+                    it.u1 = (ir + 1) * sc < blocks ? (ir + 1) * sc : blocks;
+                    b.items.push_back(it);
+                    ++ir;
+                }
+            }
+        }
+    }
+    for (int t = 0; t < B; ++t)
+        for (int c = 0; c < b.traj[t].Nc; ++c) {
+            EngineItem it;
+            it.kind = kItemProject; it.traj = t; it.tile = c; it.slot = 0; it.u0 = 0; it.u1 = 0;
+            b.items.push_back(it);
+        }
+}
+
+int validate_batch(sparkling_ctx *ctx, int32_t B, const int64_t *off, const void *K, int K_dtype,
+                   int32_t Ns, const sparkling_grid *grids, const double *eta,
+                   const sparkling_proj *proj, int acc)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    int s;
+    if (B < 1) return fail(ctx, SPARKLING_E_INVAL, "B = %d must be >= 1", B);
+    if (!off || !K || !grids || !eta || !proj)
+        return fail(ctx, SPARKLING_E_INVAL, "traj_off, K, grids, eta and proj are required");
+    if ((s = validate_dtype(ctx, K_dtype, "K"))) return s;
+    if (acc != SPARKLING_ACC_KAHAN32 && acc != SPARKLING_ACC_FP64)
+        return fail(ctx, SPARKLING_E_INVAL, "acc %d is not KAHAN32/FP64", acc);
+    if (Ns < 1 || Ns > 65536) return fail(ctx, SPARKLING_E_INVAL, "Ns = %d out of range", Ns);
+    if (off[0] != 0) return fail(ctx, SPARKLING_E_INVAL, "traj_off[0] must be 0");
+    for (int t = 0; t < B; ++t) {
+        const int64_t N = off[t + 1] - off[t];
+        if (N < 2 || N % Ns != 0 || N > ((int64_t)1 << 31) - kTile)
+            return fail(ctx, SPARKLING_E_INVAL,
+                        "trajectory %d has %lld samples: need >= 2, a multiple of Ns = %d", t,
+                        (long long)N, Ns);
+        if ((s = validate_grid(ctx, &grids[t], true))) return s;
+        if ((s = validate_proj(ctx, &proj[t], Ns))) return s;
+        if (proj[t].tol > 0)
+            return fail(ctx, SPARKLING_E_INVAL, "converged mode is not available in the batched step");
+        if (!std::isfinite(eta[t])) return fail(ctx, SPARKLING_E_INVAL, "eta[%d] not finite", t);
+    }
+    return SPARKLING_OK;
+}
+
+// Device work of one batched step on `st`: reset the counters, pack the
+// samples and the densities, run the engine.
+int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_grid *grids,
+                      int acc, cudaStream_t st)
+{
+    sparkling_ctx::Batch &b = ctx->batch;
+    const int B = b.B;
+    const int64_t Ntot = b.off[B];
+    CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0, (size_t)(B + 1) * sizeof(unsigned int), st));
+    CK(launch_pack_positions(K, K_dtype, Ntot, at<float4>(ctx, b.o_pos), ctx->d_status, ctx->sms, st));
+    for (int t = 0; t < B; ++t)
+        CK(launch_pack_grid(grids[t].rho, grids[t].n[0], grids[t].n[1], grids[t].n[2],
+                            b.traj[t].gxp, grids[t].lo, grids[t].hi, at<float>(ctx, b.o_rho[t]),
+                            at<float>(ctx, b.o_coords[t]), ctx->d_status, ctx->sms, st));
+    EngineArgs e;
+    e.traj = at<EngineTraj>(ctx, b.o_traj);
+    e.items = at<EngineItem>(ctx, b.o_items);
+    e.n_items = (int32_t)b.items.size();
+    e.proj_in_smem = b.proj_in_smem ? 1 : 0;
+    e.pos = at<float4>(ctx, b.o_pos);
+    e.K = K;
+    e.part = at<dacc4>(ctx, b.o_part);
+    e.queue = at<unsigned int>(ctx, b.o_cnt);
+    e.done = e.queue + 1;
+    e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
+    e.status = ctx->d_status;
+    CK(launch_engine(e, acc, K_dtype, b.ctas, st));
+    return SPARKLING_OK;
+}
+
+} // namespace
+
 // Lets other translation units of the library (noalloc.cu) report a failure
 // through sparkling_last_error(NULL).
 void sparkling_set_thread_error(const char *msg) { g_err = msg; }
@@ -454,6 +752,9 @@ SPARKLING_API void sparkling_destroy(sparkling_ctx *ctx)
     if (ctx->inited) {
         cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
+        if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+        if (ctx->h_traj) cudaFreeHost(ctx->h_traj);
         cudaFree(ctx->ws);
         cudaFree(ctx->h_K);
         cudaFree(ctx->h_rho);
@@ -591,6 +892,128 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
     return SPARKLING_OK;
 }
 
+SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const int64_t *traj_off,
+                                         void *K, int K_dtype, int32_t Ns,
+                                         const sparkling_grid *grids, const double *eta,
+                                         const sparkling_proj *proj, int acc, int flags,
+                                         void *stream)
+{
+    int s;
+    if ((s = validate_batch(ctx, B, traj_off, K, K_dtype, Ns, grids, eta, proj, acc))) return s;
+    if ((s = lazy_init(ctx))) return s;
+    if (!is_device_ptr(K)) return fail(ctx, SPARKLING_E_INVAL, "K must be device memory");
+    for (int t = 0; t < B; ++t)
+        if (!is_device_ptr(grids[t].rho))
+            return fail(ctx, SPARKLING_E_INVAL, "grids[%d].rho must be device memory", t);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sparkling_ctx::Batch &b = ctx->batch;
+    std::vector<int64_t> off(traj_off, traj_off + B + 1);
+    std::vector<int32_t> dims;
+    for (int t = 0; t < B; ++t)
+        for (int a = 0; a < 3; ++a) dims.push_back(grids[t].n[a]);
+    const int occ = engine_ctas_per_sm(acc, K_dtype);
+    if (occ < 1) {
+        cudaGetLastError();
+        return fail(ctx, SPARKLING_E_CUDA, "engine kernel cannot be resident");
+    }
+    const int ctas = ctx->sms * occ;
+    const bool same = b.valid && b.B == B && b.Ns == Ns && b.acc == acc && b.dtype == K_dtype &&
+                      b.ctas == ctas && b.items_per_cta == ctx->items_per_cta && b.off == off &&
+                      b.dims == dims;
+    if (!same) {
+        if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+        b = sparkling_ctx::Batch();
+        b.B = B; b.Ns = Ns; b.acc = acc; b.dtype = K_dtype; b.ctas = ctas;
+        b.items_per_cta = ctx->items_per_cta;
+        b.off = off; b.dims = dims;
+        build_work_list(b, off, grids, ctas, ctx->items_per_cta);
+        Carve cv;
+        b.o_pos = cv.take((size_t)off[B] * sizeof(float4));
+        for (int t = 0; t < B; ++t) {
+            b.o_rho.push_back(cv.take((size_t)b.traj[t].ny * b.traj[t].nz * b.traj[t].gxp * sizeof(float)));
+            b.o_coords.push_back(cv.take(((size_t)b.traj[t].gxp + b.traj[t].ny + b.traj[t].nz) * sizeof(float)));
+        }
+        b.o_traj = cv.take((size_t)B * sizeof(EngineTraj));
+        b.o_items = cv.take(b.items.size() * sizeof(EngineItem));
+        b.o_cnt = cv.take((size_t)(B + 1) * sizeof(unsigned int));
+        int64_t parts = 0;
+        for (int t = 0; t < B; ++t) parts += (int64_t)b.traj[t].tiles * b.traj[t].slots;
+        b.o_part = cv.take((size_t)parts * kTile * sizeof(dacc4));
+        b.proj_in_smem = project_state_bytes(Ns) <= engine_proj_smem_limit();
+        if (!b.proj_in_smem) b.o_gstate = cv.take((size_t)ctas * project_state_bytes(Ns));
+        b.end = cv.off;
+        b.kernels_per_step = 2 + B;   // pack positions, B grid packs, engine
+        if ((s = ensure_ws(ctx, b.end))) { b.valid = false; return s; }
+        CK(cudaMemcpyAsync(at<EngineItem>(ctx, b.o_items), b.items.data(),
+                           b.items.size() * sizeof(EngineItem), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        b.valid = true;
+    }
+    // Per-call trajectory descriptors (step sizes, constraints, grid origin).
+    if (ctx->h_traj_cap < (size_t)B) {
+        CK(cudaStreamSynchronize(st));
+        if (ctx->h_traj) cudaFreeHost(ctx->h_traj);
+        ctx->h_traj = nullptr;
+        ctx->h_traj_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->h_traj, (size_t)B * sizeof(EngineTraj)));
+        ctx->h_traj_cap = B;
+    } else {
+        CK(cudaStreamSynchronize(st));   // the staging buffer may still feed a previous copy
+    }
+    for (int t = 0; t < B; ++t) {
+        EngineTraj tr = b.traj[t];
+        const double h = (grids[t].hi - grids[t].lo) / grids[t].n[0];
+        tr.x0 = grids[t].lo + 0.5 * h;
+        tr.hx = (float)h;
+        tr.rho = at<float>(ctx, b.o_rho[t]);
+        tr.coords = at<float>(ctx, b.o_coords[t]);
+        tr.eta = eta[t];
+        tr.alpha = proj[t].alpha; tr.beta = proj[t].beta; tr.box = proj[t].box;
+        for (int c = 0; c < 3; ++c) tr.pin[c] = proj[t].pin[c];
+        tr.pin_index = proj[t].pin_index < 0 ? -1 : proj[t].pin_index;
+        tr.n_iter = proj[t].n_iter;
+        ctx->h_traj[t] = tr;
+    }
+    CK(cudaMemcpyAsync(at<EngineTraj>(ctx, b.o_traj), ctx->h_traj, (size_t)B * sizeof(EngineTraj),
+                       cudaMemcpyHostToDevice, st));
+
+    // Graph replay when asked for and the call matches the captured one.
+    std::vector<const void *> key;
+    key.push_back(K);
+    key.push_back(ctx->ws);
+    for (int t = 0; t < B; ++t) key.push_back(grids[t].rho);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    const bool use_graph = (flags & SPARKLING_BATCH_GRAPH) && cap == cudaStreamCaptureStatusNone;
+    LaunchScope ls(ctx, SPARKLING_KERNEL_ENGINE, st);
+    if (use_graph && b.exec && b.graph_key == key) {
+        CK(cudaGraphLaunch(b.exec, st));
+    } else if (use_graph && b.eager_calls > 0) {
+        // Capture (which records without executing) on a private stream --
+        // the legacy default stream cannot be captured -- and launch the
+        // graph on the caller's stream.
+        if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+        if (!ctx->cap_stream)
+            CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int w = batch_device_work(ctx, K, K_dtype, grids, acc, ctx->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (w) { if (g) cudaGraphDestroy(g); return w; }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b.exec = nullptr; return cuda_fail(ctx, e, "cudaGraphInstantiate"); }
+        b.graph_key = key;
+        CK(cudaGraphLaunch(b.exec, st));
+    } else {
+        if ((s = batch_device_work(ctx, K, K_dtype, grids, acc, st))) return s;
+        ++b.eager_calls;
+    }
+    ls.done((int)b.kernels_per_step);
+    return SPARKLING_OK;
+}
+
 SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dtype, int64_t Nc,
                                       int64_t Ns, const sparkling_grid *grid, const float *rho_host,
                                       int acc, double eta, const sparkling_proj *proj, void *stream)
@@ -675,6 +1098,44 @@ SPARKLING_API int sparkling_kernel_times(sparkling_ctx *ctx, double *ms_out, int
     }
     if (reset)
         for (int k = 0; k < SPARKLING_KERNEL_COUNT; ++k) { ctx->ms[k] = 0; ctx->nlaunch[k] = 0; }
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    ctx->autotune = enable != 0;
+    if (enable < 0) {   // forget the choices made so far
+        ctx->attr_choice.clear();
+        ctx->rep_choice[0] = ctx->rep_choice[1] = -1;
+        ctx->tune_log.clear();
+        ctx->autotune = true;
+    }
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len)
+{
+    if (!ctx || !buf || len < 1) return SPARKLING_E_INVAL;
+    std::string r = ctx->tune_log;
+    for (const auto &kv : ctx->attr_choice) {
+        char line[128];
+        snprintf(line, sizeof line, "chosen attraction acc=%d gxp=%d: threads=%d\n",
+                 (int)(kv.first >> 20), (int)(kv.first & ((1 << 20) - 1)),
+                 attr_variant_threads(kv.second));
+        r += line;
+    }
+    for (int acc = 0; acc < 2; ++acc)
+        if (ctx->rep_choice[acc] >= 0) {
+            char line[128];
+            snprintf(line, sizeof line, "chosen repulsion acc=%d: threads=%d unroll=%d\n", acc,
+                     rep_variant_threads(ctx->rep_choice[acc]),
+                     rep_variant_unroll(ctx->rep_choice[acc]));
+            r += line;
+        }
+    const size_t n = std::min<size_t>(r.size(), (size_t)len - 1);
+    std::memcpy(buf, r.data(), n);
+    buf[n] = 0;
     return SPARKLING_OK;
 }
 

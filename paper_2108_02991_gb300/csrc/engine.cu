@@ -1,0 +1,231 @@
+// Persistent engine: one launch of a whole projected-gradient step (eq.
+// proj_grad_descent, the inner loop of Algorithm 1) for a batch of
+// independent trajectories of uneven size.
+//
+// The host builds a work list (api.cu): for every trajectory and every tile
+// of 1024 targets, attraction items (a run of grid rows) and repulsion items
+// (a run of source blocks), then one projection item per shot.  Every CTA of
+// a single wave pulls the next item from a global counter.  Consecutive
+// attraction and repulsion items land on different CTAs, so each SM runs
+// SFU-bound attraction CTAs and issue-bound repulsion CTAs side by side.
+//
+// A pair item writes the FP64 partial sums of its tile into its own slot and
+// then bumps its trajectory's completion counter.  A projection item waits
+// (bounded) until its trajectory's counter reaches the number of pair items,
+// adds the slots of each sample in a fixed order (A - R/N), steps
+// k = K - eta G and projects the shot in place.  Because every item owns its
+// slot and the slots are added in a fixed order, results do not depend on
+// which CTA ran which item.
+//
+// All items are dispensed in list order and all pair items precede all
+// projection items, so when a CTA waits on a trajectory every item it waits
+// for is already running on another CTA: the wait always ends.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "kernels.h"
+#include "pair_dev.cuh"
+#include "project_dev.cuh"
+#include "ptx.cuh"
+
+namespace sparkling {
+
+namespace {
+
+constexpr size_t kUnionBytes = (size_t)kAccBytes + (size_t)kStages * kStageFloats * sizeof(float);
+constexpr size_t kHeadBytes = 128;   // mbarriers + item broadcast
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Every thread's partial writes are made visible device-wide, then one
+// thread counts the item as done.
+__device__ __forceinline__ void mark_done(unsigned int *done)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        atomicAdd(done, 1u);
+}
+
+// Bounded wait until *done >= target; false (and the timeout status bit) if
+// it does not happen within kWaitCycles.
+__device__ bool wait_done(const unsigned int *done, unsigned int target, int *status, int *flag)
+{
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire(done) < target) {
+            const long long t0 = clock64();
+            while (ld_acquire(done) < target) {
+                if (clock64() - t0 > kWaitCycles) {
+                    atomicOr(status, kDevTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    const bool ok = *flag != 0;
+    __syncthreads();
+    __threadfence();
+    return ok;
+}
+
+__device__ __forceinline__ AttrArgs attr_args(const EngineTraj &t, const EngineArgs &e)
+{
+    AttrArgs a;
+    a.tgt = e.pos + t.off;
+    a.N = t.N;
+    a.rho = t.rho;
+    a.coords = t.coords;
+    a.gxp = t.gxp; a.ny = t.ny; a.nz = t.nz;
+    a.rows_per_stage = t.rows_per_stage;
+    a.x0 = t.x0;
+    a.hx = t.hx;
+    a.sp.units = 0; a.sp.per_tile = 0; a.sp.ctas = 1;
+    a.sp.slots = t.slots;
+    a.part = e.part + t.part_off;
+    a.status = e.status;
+    return a;
+}
+
+__device__ __forceinline__ RepArgs rep_args(const EngineTraj &t, const EngineArgs &e)
+{
+    RepArgs r;
+    r.pos = e.pos + t.off;
+    r.N = t.N;
+    r.sp.units = 0; r.sp.per_tile = 0; r.sp.ctas = 1;
+    r.sp.slots = t.slots;
+    r.part = e.part + t.part_off;
+    r.status = e.status;
+    return r;
+}
+
+template <int ACC, typename KT>
+__global__ void __launch_bounds__(kThreads, 3) engine_kernel(const EngineArgs e)
+{
+    extern __shared__ __align__(128) unsigned char esm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(esm);
+    int *bcast = reinterpret_cast<int *>(esm + 64);
+    unsigned char *region = esm + kHeadBytes;
+    void *accbase = region;
+    float *stage = reinterpret_cast<float *>(region + kAccBytes);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s)
+            mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t consumed = 0;
+    for (;;) {
+        if (threadIdx.x == 0)
+            bcast[0] = (int)atomicAdd(e.queue, 1u);
+        __syncthreads();
+        const int idx = bcast[0];
+        __syncthreads();
+        if (idx >= e.n_items)
+            break;
+        const EngineItem item = e.items[idx];
+        const EngineTraj &tr = e.traj[item.traj];
+        if (item.kind == kItemAttraction) {
+            const AttrArgs a = attr_args(tr, e);
+            if (!attraction_segment<ACC, false, kThreads>(a, item.tile, item.u0, item.u1, item.slot, stage,
+                                                bars, accbase, consumed))
+                return;
+            mark_done(e.done + item.traj);
+        } else if (item.kind == kItemRepulsion) {
+            const RepArgs r = rep_args(tr, e);
+            if (!repulsion_segment<ACC, false, kThreads, 2>(r, item.tile, item.u0, item.u1, item.slot,
+                                               reinterpret_cast<float4 *>(stage), bars, accbase,
+                                               consumed))
+                return;
+            mark_done(e.done + item.traj);
+        } else {
+            if (!wait_done(e.done + item.traj, (unsigned int)tr.n_pair_items, e.status, bcast + 1))
+                return;
+            const int Ns = tr.Ns;
+            double *base = e.proj_in_smem ? reinterpret_cast<double *>(region)
+                                          : e.gstate + (size_t)blockIdx.x * 18 * (size_t)Ns;
+            const Arrays A = carve(base, Ns);
+            ShotParams sp;
+            sp.Ns = Ns;
+            sp.alpha = tr.alpha; sp.beta = tr.beta; sp.box = tr.box;
+            sp.tol = 0.0; sp.margin = 0.0;
+            for (int c = 0; c < 3; ++c) sp.pin[c] = tr.pin[c];
+            sp.pin_index = tr.pin_index; sp.n_iter = tr.n_iter; sp.check_every = 0;
+            sp.viol = nullptr; sp.notconv = nullptr;
+            const int64_t first = (int64_t)item.tile * Ns;          // local sample index
+            KT *K = static_cast<KT *>(e.K) + 3 * (tr.off + first);
+            const dacc4 *part = e.part + tr.part_off;
+            const double invN = 1.0 / (double)tr.N;
+            const double eta = tr.eta;
+            const int slots = tr.slots, ach = tr.a_chunks;
+            auto loadk = [&](int m, double *kv) {
+                const int64_t i = first + m;
+                const int64_t tile = i / kTile, l = i - tile * kTile;
+                const dacc4 *p = part + tile * slots * kTile + l;
+                double g[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
+                for (int s = 0; s < slots; ++s) {
+                    const double2 xy = __ldcg(reinterpret_cast<const double2 *>(p + s * kTile));
+                    const double zz = __ldcg(reinterpret_cast<const double *>(p + s * kTile) + 2);
+                    if (s < ach) { g[0] += xy.x; g[1] += xy.y; g[2] += zz; }
+                    else { r[0] += xy.x; r[1] += xy.y; r[2] += zz; }
+                }
+                for (int c = 0; c < 3; ++c)
+                    kv[c] = (double)K[3 * m + c] - eta * (g[c] - r[c] * invN);
+            };
+            if (sizeof(KT) == 4)
+                project_shot_mixed<KT>(carve_f(reinterpret_cast<float *>(base), Ns), K, sp, loadk);
+            else
+                project_shot<KT>(A, K, sp, loadk);
+            // The projection state may share memory with the stage buffers:
+            // order its ordinary stores before later bulk copies (async proxy).
+            fence_proxy_async_smem();
+            __syncthreads();
+        }
+    }
+}
+
+template <int ACC, typename KT>
+void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT>); }
+
+void *pick_engine(int acc, int dtype)
+{
+    if (acc == 0) return dtype == 0 ? engine_fn<0, float>() : engine_fn<0, double>();
+    return dtype == 0 ? engine_fn<1, float>() : engine_fn<1, double>();
+}
+
+} // namespace
+
+size_t engine_smem_bytes() { return kHeadBytes + kUnionBytes; }
+
+size_t engine_proj_smem_limit() { return kUnionBytes; }
+
+int engine_ctas_per_sm(int acc, int dtype)
+{
+    void *fn = pick_engine(acc, dtype);
+    const size_t smem = engine_smem_bytes();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int ctas, cudaStream_t st)
+{
+    void *fn = pick_engine(acc, dtype);
+    void *args[] = {const_cast<EngineArgs *>(&e)};
+    return cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(kThreads), args, engine_smem_bytes(), st);
+}
+
+} // namespace sparkling

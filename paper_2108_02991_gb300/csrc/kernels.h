@@ -6,9 +6,8 @@
 
 namespace sparkling {
 
-constexpr int kThreads = 256;          // threads per CTA of the pair kernels
-constexpr int kTargetsPerThread = 4;   // register-blocked targets per thread
-constexpr int kTile = kThreads * kTargetsPerThread;  // targets per tile
+constexpr int kTile = 1024;            // targets per tile (one CTA's targets)
+constexpr int kThreads = 256;          // threads per CTA of the engine and the default shapes
 constexpr int kStages = 3;             // TMA pipeline depth
 constexpr int kStageFloats = 4096;     // 16 KB per stage
 constexpr int kSrcBlock = kStageFloats / 4;  // repulsion sources per stage (float4)
@@ -98,18 +97,29 @@ struct CombineArgs {
     double2 *energy_blocks;  // energy mode: per-block (sum ea, sum er)
 };
 
-// Launchers (pairs.cu).  dtype: 0 float, 1 double.
+// Tile shapes of the pair kernels, chosen per problem by the autotuner
+// (api.cu).  Every shape keeps kTile targets per CTA; it trades threads per
+// CTA against targets held in registers per thread (and, for the repulsion,
+// the unroll of the source loop).
+constexpr int kAttrVariants = 3;       // threads 128 / 256 / 512 (8 / 4 / 2 targets each)
+constexpr int kRepVariants = 5;        // (threads, unroll) 128x2, 256x1, 256x2, 256x4, 512x2
+constexpr int kAttrDefault = 1, kRepDefault = 2;
+int attr_variant_threads(int v);
+int rep_variant_threads(int v);
+int rep_variant_unroll(int v);
+
+// Launchers (pairs.cu, repulsion.cu).  dtype: 0 float, 1 double.
 cudaError_t launch_pack_positions(const void *K, int dtype, int64_t N, float4 *out, int *status,
                                   int sms, cudaStream_t st);
 cudaError_t launch_pack_grid(const float *rho, int nx, int ny, int nz, int gxp, double lo,
                              double hi, float *rho_out, float *coords, int *status, int sms,
                              cudaStream_t st);
 size_t attraction_smem_bytes(int gxp);
-int attraction_ctas_per_sm(int acc, bool energy, int gxp);
-cudaError_t launch_attraction(const AttrArgs &a, int acc, bool energy, cudaStream_t st);
+int attraction_ctas_per_sm(int acc, bool energy, int variant);
+cudaError_t launch_attraction(const AttrArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 size_t repulsion_smem_bytes();
-int repulsion_ctas_per_sm(int acc, bool energy);
-cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, cudaStream_t st);
+int repulsion_ctas_per_sm(int acc, bool energy, int variant);
+cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st);
 int energy_blocks(int64_t N);
 cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream_t st);
@@ -134,5 +144,54 @@ bool project_state_in_smem(int Ns);
 int project_block(int Ns);
 int project_ctas_per_sm(int dtype, int Ns);
 cudaError_t launch_project(const ProjArgs &p, int dtype, int grid, cudaStream_t st);
+
+// Persistent engine (engine.cu): one launch runs a work list of pair items
+// (attraction or repulsion of one target tile against a run of grid rows or
+// source blocks) for any number of trajectories, followed by per-shot
+// projection items that wait until their trajectory's pair items are done.
+struct EngineTraj {
+    int64_t off;             // first sample of the trajectory in K / pos
+    int64_t N;               // samples
+    int64_t part_off;        // first partial (dacc4 units) of this trajectory
+    const float *rho;        // density rows padded to gxp, 16-byte aligned rows
+    const float *coords;     // x[gxp], y[ny], z[nz]
+    double x0;               // lo + h/2
+    double eta;              // step size (G units)
+    double alpha, beta, box;
+    double pin[3];
+    float hx;
+    int32_t Nc, Ns;
+    int32_t gxp, ny, nz, rows_per_stage;
+    int32_t tiles, slots, a_chunks;   // slots per tile: a_chunks attraction + the rest repulsion
+    int32_t n_pair_items;
+    int32_t pin_index, n_iter;
+};
+
+constexpr int kItemAttraction = 0, kItemRepulsion = 1, kItemProject = 2;
+
+struct EngineItem {
+    int32_t kind, traj;
+    int32_t tile, slot;      // pair items: target tile and partial slot; project: shot, -
+    int64_t u0, u1;          // pair items: grid-row or source-block range
+};
+
+struct EngineArgs {
+    const EngineTraj *traj;
+    const EngineItem *items;
+    int32_t n_items;
+    int32_t proj_in_smem;    // projection state fits in the shared-memory union
+    const float4 *pos;       // packed samples of all trajectories
+    void *K;                 // [sum N][3], updated in place by the projection items
+    dacc4 *part;
+    unsigned int *queue;     // next item (reset to 0 before every launch)
+    unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
+    double *gstate;          // per-CTA projection state when it is not in shared memory
+    int *status;
+};
+
+size_t engine_smem_bytes();
+size_t engine_proj_smem_limit();     // largest 18*Ns*8 that fits the shared-memory union
+int engine_ctas_per_sm(int acc, int dtype);
+cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int ctas, cudaStream_t st);
 
 } // namespace sparkling

@@ -156,8 +156,8 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     if ((s = scratch_for_current_device(&base, &sms))) return s;
     if (!on_device(K) || !on_device(G) || !on_device(grid->rho))
         return noalloc_fail(SPARKLING_E_INVAL, "K, G and grid->rho must be device memory");
-    const int occ_a = attraction_ctas_per_sm(acc, false, gxp);
-    const int occ_r = repulsion_ctas_per_sm(acc, false);
+    const int occ_a = attraction_ctas_per_sm(acc, false, kAttrDefault);
+    const int occ_r = repulsion_ctas_per_sm(acc, false, kRepDefault);
     if (occ_a < 1 || occ_r < 1) {
         cudaGetLastError();
         return noalloc_fail(SPARKLING_E_CUDA, "pair kernels cannot be resident");
@@ -202,10 +202,10 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     aa.hx = (float)((grid->hi - grid->lo) / nx);
     aa.x0 = grid->lo + 0.5 * ((grid->hi - grid->lo) / nx);
     aa.sp = spa; aa.part = part_a; aa.status = status;
-    NA_CK(launch_attraction(aa, acc, false, st));
+    NA_CK(launch_attraction(aa, acc, false, kAttrDefault, st));
     RepArgs ra;
     ra.pos = pos; ra.N = N; ra.sp = spr; ra.part = part_r; ra.status = status;
-    NA_CK(launch_repulsion(ra, acc, false, st));
+    NA_CK(launch_repulsion(ra, acc, false, kRepDefault, st));
     CombineArgs cb;
     cb.N = N; cb.part_a = part_a; cb.part_r = part_r; cb.spa = spa; cb.spr = spr;
     cb.G = G; cb.A = nullptr; cb.R = nullptr; cb.G64 = nullptr;

@@ -28,6 +28,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "pair_dev.cuh"
 #include "ptx.cuh"
 
 namespace sparkling {
@@ -82,217 +83,12 @@ __global__ void pack_grid_kernel(const float *__restrict__ rho, int nx, int ny, 
         atomicOr(status, kDevNonFinite);
 }
 
-// Wait for the stages a CTA issued but did not consume, so that no bulk copy
-// is still writing into shared memory when the CTA exits early.
-__device__ void drain_stages(uint64_t *bars, uint32_t first, uint32_t count, int *status)
-{
-    if (threadIdx.x == 0)
-        for (uint32_t g = first; g < first + count; ++g)
-            mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1, status);
-    __syncthreads();
-}
+// Resident CTAs the launch bounds ask for: 768 threads per SM at 128/256
+// threads per CTA (registers <= 80), 1024 at 512 (registers <= 64).
+constexpr int min_ctas(int nt) { return nt >= 512 ? 2 : 768 / nt; }
 
-// Per-thread accumulators in shared memory, one column per thread (a warp
-// touches consecutive words).  ACC 0: compensated FP32 (value + TwoSum error
-// term); ACC 1: FP64.  Both take 8 bytes per accumulated value.
-template <int ACC> struct SmemAcc;
-
-template <> struct SmemAcc<0> {
-    float *p;
-    __device__ SmemAcc(void *base, int tid) : p(static_cast<float *>(base) + tid) {}
-    __device__ void zero(int nv)
-    {
-        for (int v = 0; v < 2 * nv; ++v) p[v * kThreads] = 0.f;
-    }
-    __device__ __forceinline__ void add(int v, float x)
-    {
-        float s = p[(2 * v) * kThreads], c = p[(2 * v + 1) * kThreads], t, e;
-        two_sum(s, x, t, e);
-        p[(2 * v) * kThreads] = t;
-        p[(2 * v + 1) * kThreads] = c + e;
-    }
-    __device__ double value(int v) const
-    {
-        return (double)p[(2 * v) * kThreads] + (double)p[(2 * v + 1) * kThreads];
-    }
-};
-
-template <> struct SmemAcc<1> {
-    double *p;
-    __device__ SmemAcc(void *base, int tid) : p(static_cast<double *>(base) + tid) {}
-    __device__ void zero(int nv)
-    {
-        for (int v = 0; v < nv; ++v) p[v * kThreads] = 0.0;
-    }
-    __device__ __forceinline__ void add(int v, float x) { p[v * kThreads] += (double)x; }
-    __device__ double value(int v) const { return p[v * kThreads]; }
-};
-
-constexpr int kAccBytes = kTargetsPerThread * 3 * 8 * kThreads;   // 24 KB per CTA
-
-// NR grid rows (1 or 2) against the thread's T targets.  The rows share the
-// x coordinates, so one dx = kx - x_q feeds NR pairs.  x_q is rebuilt as
-// lo + (q + 1/2) h: kxp = kx - lo - h/2 (rounded once from double) and
-// dx = kxp - q h with one FFMA per group of 4 points.  Row sums are FP32 and
-// are added into the stage accumulators st[t][0..NV).
-template <bool ENERGY, int NR>
-__device__ __forceinline__ void attr_rows(const float *rows, int gxp, const float *kxp,
-                                          const float *ky, const float *kz, const float *yr,
-                                          const float *zr, float h, float (*st)[3])
-{
-    constexpr int T = kTargetsPerThread;
-    float s2[NR][T], sw[NR][T], sx[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const float dy = ky[t] - yr[r], dz = kz[t] - zr[r];
-            s2[r][t] = fmaf(dy, dy, fmaf(dz, dz, kEps2));
-            sw[r][t] = 0.f;
-        }
-        sx[t] = 0.f;
-    }
-    const float mh = -h, h2 = 2.f * h, h3 = 3.f * h;
-    const int n4 = gxp >> 2;
-    float qf = 0.f;
-#pragma unroll (NR == 1 ? 2 : 1)
-    for (int g4 = 0; g4 < n4; ++g4) {
-        float4 w[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            w[r] = reinterpret_cast<const float4 *>(rows + r * gxp)[g4];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            float dx[4];
-            dx[0] = fmaf(qf, mh, kxp[t]);
-            dx[1] = dx[0] - h;
-            dx[2] = dx[0] - h2;
-            dx[3] = dx[0] - h3;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const float rho = j == 0 ? w[r].x : j == 1 ? w[r].y : j == 2 ? w[r].z : w[r].w;
-                    const float r2 = fmaf(dx[j], dx[j], s2[r][t]);
-                    const float wt = rho * rsqrt_sfu(r2);
-                    if (ENERGY) {
-                        sw[r][t] = fmaf(wt, r2, sw[r][t]);     // rho * |d|
-                    } else {
-                        sw[r][t] += wt;
-                        sx[t] = fmaf(wt, dx[j], sx[t]);
-                    }
-                }
-            }
-        }
-        qf += 4.f;
-    }
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        if (ENERGY) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) st[t][0] += sw[r][t];
-        } else {
-            st[t][0] += sx[t];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                st[t][1] = fmaf(ky[t] - yr[r], sw[r][t], st[t][1]);
-                st[t][2] = fmaf(kz[t] - zr[r], sw[r][t], st[t][2]);
-            }
-        }
-    }
-}
-
-template <int ACC, bool ENERGY>
-__device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, int64_t r1,
-                                   int slot, float *stage, uint64_t *bars, void *accbase,
-                                   uint32_t &consumed)
-{
-    constexpr int T = kTargetsPerThread;
-    constexpr int NV = ENERGY ? 1 : 3;
-    const int tid = threadIdx.x;
-    float kxp[T], ky[T], kz[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tile * kTile + t * kThreads + tid;
-        const float4 p = i < a.N ? a.tgt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        kxp[t] = (float)((double)p.x - a.x0);
-        ky[t] = p.y;
-        kz[t] = p.z;
-    }
-    SmemAcc<ACC> acc(accbase, tid);
-    acc.zero(T * NV);
-    const int R = a.rows_per_stage;
-    const uint32_t nst = (uint32_t)((r1 - r0 + R - 1) / R);
-    const int gxp = a.gxp;
-
-    auto issue = [&](uint32_t s) {
-        const int64_t rs = r0 + (int64_t)s * R;
-        const int64_t re = rs + R < r1 ? rs + R : r1;
-        const uint32_t g = consumed + s;
-        bulk_load(stage + (g % kStages) * kStageFloats, a.rho + rs * gxp,
-                  (uint32_t)((re - rs) * gxp * sizeof(float)), &bars[g % kStages]);
-    };
-    if (tid == 0)
-        for (uint32_t s = 0; s < nst && s < (uint32_t)kStages; ++s)
-            issue(s);
-
-    const float *ys = a.coords + gxp;
-    const float *zs = ys + a.ny;
-    for (uint32_t s = 0; s < nst; ++s) {
-        const uint32_t g = consumed + s;
-        const bool ok = mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1, a.status);
-        if (__syncthreads_or(!ok)) {
-            // Stage s and the ones issued after it may still be in flight.
-            const uint32_t left = nst - s;
-            drain_stages(bars, g, left < (uint32_t)kStages ? left : (uint32_t)kStages, a.status);
-            return false;
-        }
-        const float *buf = stage + (g % kStages) * kStageFloats;
-        const int64_t rs = r0 + (int64_t)s * R;
-        const int nrows = (int)((rs + R < r1 ? rs + R : r1) - rs);
-        int iy = (int)(rs % a.ny), iz = (int)(rs / a.ny);
-        float st[T][3];
-#pragma unroll
-        for (int t = 0; t < T; ++t) st[t][0] = st[t][1] = st[t][2] = 0.f;
-        int rr = 0;
-        for (; rr + 1 < nrows; rr += 2) {
-            float yr[2], zr[2];
-            yr[0] = ys[iy]; zr[0] = zs[iz];
-            if (++iy == a.ny) { iy = 0; ++iz; }
-            yr[1] = ys[iy]; zr[1] = zs[iz];
-            if (++iy == a.ny) { iy = 0; ++iz; }
-            attr_rows<ENERGY, 2>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
-        }
-        if (rr < nrows) {
-            float yr[1] = {ys[iy]}, zr[1] = {zs[iz]};
-            attr_rows<ENERGY, 1>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
-        }
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc.add(t * NV + v, st[t][v]);
-        __syncthreads();   // every thread is done with this buffer
-        if (tid == 0 && s + kStages < nst) {
-            fence_proxy_async_smem();
-            issue(s + kStages);
-        }
-    }
-    consumed += nst;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int l = t * kThreads + tid;
-        if (tile * kTile + l < a.N) {
-            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, acc.value(t))
-                             : make_dacc4(acc.value(3 * t), acc.value(3 * t + 1),
-                                          acc.value(3 * t + 2), 0.0);
-            a.part[(tile * a.sp.slots + slot) * kTile + l] = v;
-        }
-    }
-    return true;
-}
-
-template <int ACC, bool ENERGY>
-__global__ void __launch_bounds__(kThreads, 3) attraction_kernel(const AttrArgs a)
+template <int ACC, bool ENERGY, int NT>
+__global__ void __launch_bounds__(NT, min_ctas(NT)) attraction_kernel(const AttrArgs a)
 {
     extern __shared__ __align__(128) float smem[];
     void *accbase = smem;                                     // kAccBytes
@@ -313,157 +109,11 @@ __global__ void __launch_bounds__(kThreads, 3) attraction_kernel(const AttrArgs 
         const int64_t r0 = u - tile * rows;
         const int64_t r1 = rows < r0 + (uend - u) ? rows : r0 + (uend - u);
         const int slot = (int)(blockIdx.x - split_cta_of(a.sp, tile * rows));
-        if (!attraction_segment<ACC, ENERGY>(a, tile, r0, r1, slot, stage, bars, accbase,
+        if (!attraction_segment<ACC, ENERGY, NT>(a, tile, r0, r1, slot, stage, bars, accbase,
                                              consumed))
             return;
         u += r1 - r0;
     }
-}
-
-template <bool ENERGY>
-__device__ __forceinline__ void rep_pair(float kx, float ky, float kz, const float4 q, float &rx,
-                                         float &ry, float &rz)
-{
-    const float dx = kx - q.x, dy = ky - q.y, dz = kz - q.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
-    const float ri = rsqrt_sfu(r2);
-    if (ENERGY) {
-        rx = fmaf(r2, ri, rx);           // |d|
-    } else {
-        rx = fmaf(dx, ri, rx);
-        ry = fmaf(dy, ri, ry);
-        rz = fmaf(dz, ri, rz);
-    }
-}
-
-template <int ACC, bool ENERGY>
-__device__ bool repulsion_segment(const RepArgs &a, int64_t tile, int64_t b0, int64_t b1, int slot,
-                                  float4 *stage, uint64_t *bars, void *accbase,
-                                  uint32_t &consumed)
-{
-    constexpr int T = kTargetsPerThread;
-    constexpr int NV = ENERGY ? 1 : 3;
-    const int tid = threadIdx.x;
-    float kx[T], ky[T], kz[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tile * kTile + t * kThreads + tid;
-        const float4 p = i < a.N ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        kx[t] = p.x; ky[t] = p.y; kz[t] = p.z;
-    }
-    SmemAcc<ACC> acc(accbase, tid);
-    acc.zero(T * NV);
-    const uint32_t nst = (uint32_t)(b1 - b0);
-    auto count_of = [&](int64_t b) -> int {
-        const int64_t rem = a.N - b * kSrcBlock;
-        return rem < kSrcBlock ? (int)rem : kSrcBlock;
-    };
-    auto issue = [&](uint32_t s) {
-        const int64_t b = b0 + s;
-        const uint32_t g = consumed + s;
-        bulk_load(stage + (g % kStages) * kSrcBlock, a.pos + b * kSrcBlock,
-                  (uint32_t)(count_of(b) * sizeof(float4)), &bars[g % kStages]);
-    };
-    if (tid == 0)
-        for (uint32_t s = 0; s < nst && s < (uint32_t)kStages; ++s)
-            issue(s);
-    for (uint32_t s = 0; s < nst; ++s) {
-        const uint32_t g = consumed + s;
-        const bool ok = mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1, a.status);
-        if (__syncthreads_or(!ok)) {
-            // Stage s and the ones issued after it may still be in flight.
-            const uint32_t left = nst - s;
-            drain_stages(bars, g, left < (uint32_t)kStages ? left : (uint32_t)kStages, a.status);
-            return false;
-        }
-        const float4 *buf = stage + (g % kStages) * kSrcBlock;
-        const int cnt = count_of(b0 + s);
-        float rx[T], ry[T], rz[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) { rx[t] = 0.f; ry[t] = 0.f; rz[t] = 0.f; }
-        if (cnt == kSrcBlock) {
-#pragma unroll 2
-            for (int j = 0; j < kSrcBlock; ++j) {
-                const float4 q = buf[j];
-#pragma unroll
-                for (int t = 0; t < T; ++t)
-                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, rx[t], ry[t], rz[t]);
-            }
-        } else {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 q = buf[j];
-#pragma unroll
-                for (int t = 0; t < T; ++t)
-                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, rx[t], ry[t], rz[t]);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            acc.add(t * NV, rx[t]);
-            if (!ENERGY) {
-                acc.add(t * NV + 1, ry[t]);
-                acc.add(t * NV + 2, rz[t]);
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && s + kStages < nst) {
-            fence_proxy_async_smem();
-            issue(s + kStages);
-        }
-    }
-    consumed += nst;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int l = t * kThreads + tid;
-        if (tile * kTile + l < a.N) {
-            dacc4 v = ENERGY ? make_dacc4(0.0, 0.0, 0.0, acc.value(t))
-                             : make_dacc4(acc.value(3 * t), acc.value(3 * t + 1),
-                                          acc.value(3 * t + 2), 0.0);
-            a.part[(tile * a.sp.slots + slot) * kTile + l] = v;
-        }
-    }
-    return true;
-}
-
-template <int ACC, bool ENERGY>
-__global__ void __launch_bounds__(kThreads, 3) repulsion_kernel(const RepArgs a)
-{
-    extern __shared__ __align__(128) float4 smem4[];
-    void *accbase = smem4;
-    float4 *stage = smem4 + kAccBytes / sizeof(float4);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStages * kSrcBlock);
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s)
-            mbar_init(&bars[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    const int64_t per = a.sp.per_tile;
-    int64_t u = split_begin(a.sp, blockIdx.x);
-    const int64_t uend = split_begin(a.sp, blockIdx.x + 1);
-    uint32_t consumed = 0;
-    while (u < uend) {
-        const int64_t tile = u / per;
-        const int64_t b0 = u - tile * per;
-        const int64_t b1 = per < b0 + (uend - u) ? per : b0 + (uend - u);
-        const int slot = (int)(blockIdx.x - split_cta_of(a.sp, tile * per));
-        if (!repulsion_segment<ACC, ENERGY>(a, tile, b0, b1, slot, stage, bars, accbase, consumed))
-            return;
-        u += b1 - b0;
-    }
-}
-
-__device__ __forceinline__ dacc4 sum_slots(const dacc4 *part, const Split &sp, int64_t i)
-{
-    const int64_t tile = i / kTile, l = i - tile * kTile;
-    const int64_t lo = split_cta_of(sp, tile * sp.per_tile);
-    const int64_t hi = split_cta_of(sp, (tile + 1) * sp.per_tile - 1);
-    dacc4 s = make_dacc4(0.0, 0.0, 0.0, 0.0);
-    for (int64_t j = 0; j <= hi - lo; ++j) {
-        const dacc4 v = part[(tile * sp.slots + j) * kTile + l];
-        s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
-    }
-    return s;
 }
 
 template <typename OT>
@@ -551,21 +201,23 @@ cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int ACC, bool E>
-void *attraction_fn() { return reinterpret_cast<void *>(attraction_kernel<ACC, E>); }
-template <int ACC, bool E>
-void *repulsion_fn() { return reinterpret_cast<void *>(repulsion_kernel<ACC, E>); }
+template <int ACC, bool E, int NT>
+void *attraction_fn() { return reinterpret_cast<void *>(attraction_kernel<ACC, E, NT>); }
 
-void *pick_attraction(int acc, bool energy)
+template <int NT>
+void *pick_attraction_nt(int acc, bool energy)
 {
-    if (acc == 0) return energy ? attraction_fn<0, true>() : attraction_fn<0, false>();
-    return energy ? attraction_fn<1, true>() : attraction_fn<1, false>();
+    if (acc == 0) return energy ? attraction_fn<0, true, NT>() : attraction_fn<0, false, NT>();
+    return energy ? attraction_fn<1, true, NT>() : attraction_fn<1, false, NT>();
 }
 
-void *pick_repulsion(int acc, bool energy)
+void *pick_attraction(int acc, bool energy, int variant)
 {
-    if (acc == 0) return energy ? repulsion_fn<0, true>() : repulsion_fn<0, false>();
-    return energy ? repulsion_fn<1, true>() : repulsion_fn<1, false>();
+    switch (variant) {
+    case 0: return pick_attraction_nt<128>(acc, energy);
+    case 2: return pick_attraction_nt<512>(acc, energy);
+    default: return pick_attraction_nt<256>(acc, energy);
+    }
 }
 
 int grid_for(int64_t n, int threads, int sms)
@@ -598,56 +250,33 @@ cudaError_t launch_pack_grid(const float *rho, int nx, int ny, int nz, int gxp, 
     return cudaGetLastError();
 }
 
+int attr_variant_threads(int v) { return v == 0 ? 128 : (v == 2 ? 512 : 256); }
+
 size_t attraction_smem_bytes(int)
 {
     return (size_t)kAccBytes + (size_t)kStages * kStageFloats * sizeof(float) +
            kStages * sizeof(uint64_t);
 }
 
-size_t repulsion_smem_bytes()
+int attraction_ctas_per_sm(int acc, bool energy, int variant)
 {
-    return (size_t)kAccBytes + (size_t)kStages * kSrcBlock * sizeof(float4) +
-           kStages * sizeof(uint64_t);
-}
-
-int attraction_ctas_per_sm(int acc, bool energy, int gxp)
-{
-    void *fn = pick_attraction(acc, energy);
-    const size_t smem = attraction_smem_bytes(gxp);
+    void *fn = pick_attraction(acc, energy, variant);
+    const size_t smem = attraction_smem_bytes(0);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, attr_variant_threads(variant), smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
 
-int repulsion_ctas_per_sm(int acc, bool energy)
+cudaError_t launch_attraction(const AttrArgs &a, int acc, bool energy, int variant, cudaStream_t st)
 {
-    void *fn = pick_repulsion(acc, energy);
-    const size_t smem = repulsion_smem_bytes();
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess)
-        return 0;
-    return n;
-}
-
-cudaError_t launch_attraction(const AttrArgs &a, int acc, bool energy, cudaStream_t st)
-{
-    void *fn = pick_attraction(acc, energy);
+    void *fn = pick_attraction(acc, energy, variant);
     void *args[] = {const_cast<AttrArgs *>(&a)};
-    return cudaLaunchKernel(fn, dim3((unsigned)a.sp.ctas), dim3(kThreads), args,
+    return cudaLaunchKernel(fn, dim3((unsigned)a.sp.ctas), dim3(attr_variant_threads(variant)), args,
                             attraction_smem_bytes(a.gxp), st);
-}
-
-cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, cudaStream_t st)
-{
-    void *fn = pick_repulsion(acc, energy);
-    void *args[] = {const_cast<RepArgs *>(&a)};
-    return cudaLaunchKernel(fn, dim3((unsigned)a.sp.ctas), dim3(kThreads), args,
-                            repulsion_smem_bytes(), st);
 }
 
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st)

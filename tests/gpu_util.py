@@ -26,3 +26,13 @@ def assert_grad_close(gpu, ref, what="G", rel=GRAD_REL_L2, atol=GRAD_ABS):
     assert e <= rel, f"{what}: relative L2 error {e:.3e} > {rel:.1e}"
     assert m <= atol, f"{what}: max abs error {m:.3e} > {atol:.1e}"
     return e, m
+
+
+def proj_tol_f32(ref, k) -> float:
+    """Elementwise gate of a projection with FP32 output.  The FP32 output
+    rounds s (<= 2^-24 at |s| <= 1/2, doubled: 1.2e-7); the FP32 iteration
+    of the mixed-precision form works on the displacement e = s - k and the
+    duals, whose roundings (a few per iteration, accumulating over the
+    iterations) stay within 128 * 2^-24 * max|e|."""
+    e = np.abs(np.asarray(ref, np.float64) - np.asarray(k, np.float64)).max()
+    return 1.2e-7 + 128 * 2.0 ** -24 * e
