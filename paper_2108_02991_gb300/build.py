@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparkling.so")
-SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "project.cu", "noalloc.cu", "engine.cu"]
+SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "repulsion_sym.cu", "project.cu", "noalloc.cu", "engine.cu"]
 HEADERS = ["kernels.h", "ptx.cuh", "pair_dev.cuh", "project_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

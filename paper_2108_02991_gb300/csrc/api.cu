@@ -50,11 +50,15 @@ struct sparkling_ctx {
     bool autotune = true;
     std::vector<std::pair<int64_t, int>> attr_choice;   // key acc * 2^20 + gxp
     int rep_choice[2] = {-1, -1};
+    bool rep_symmetric = true;     // repulsion: symmetric kernel (else the directed shapes)
+    int occ_sym[2] = {0, 0};
     std::string tune_log;
     // batched step: cached work list, workspace layout and CUDA graph
     struct Batch {
         bool valid = false;
         int B = 0, Ns = 0, acc = -1, dtype = -1, ctas = 0, items_per_cta = 0;
+        int64_t n_pair_items = 0;
+        std::vector<double> item_pairs;   // pair count of every pair item (tuning prefix)
         std::vector<int64_t> off;
         std::vector<int32_t> dims;
         std::vector<EngineTraj> traj;
@@ -66,12 +70,14 @@ struct sparkling_ctx {
         // graph of the device work of one step (counters, packs, engine)
         cudaGraphExec_t exec = nullptr;
         std::vector<const void *> graph_key;
+        int graph_variant = -1;
         int eager_calls = 0;
     } batch;
     cudaStream_t cap_stream = nullptr;  // private stream the batched step is captured on
     EngineTraj *h_traj = nullptr;   // pinned staging of the trajectory descriptors
     size_t h_traj_cap = 0;
-    int items_per_cta = 16;         // work-list granularity (autotuned)
+    int items_per_cta = 16;         // work-list granularity
+    int engine_choice[2][2] = {{-1, -1}, {-1, -1}};   // [acc][K dtype] engine tile shape
 };
 
 namespace {
@@ -259,7 +265,7 @@ struct PairPlan {
     int64_t tiles;
     int va, vr;            // tile shapes (autotuner variants) of the two pair kernels
     Split spa, spr;
-    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_eblocks, o_g64, end;
+    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_racc, o_eblocks, o_g64, end;
 };
 
 int ensure_occupancy(sparkling_ctx *ctx)
@@ -272,7 +278,9 @@ int ensure_occupancy(sparkling_ctx *ctx)
             for (int v = 0; v < kRepVariants; ++v)
                 ctx->occ_rep[acc][e][v] = repulsion_ctas_per_sm(acc, e != 0, v);
         }
+    for (int e = 0; e < 2; ++e) ctx->occ_sym[e] = repulsion_sym_ctas_per_sm(e != 0);
     cudaGetLastError();
+    if (ctx->occ_sym[0] < 1 || ctx->occ_sym[1] < 1) ctx->rep_symmetric = false;
     for (int acc = 0; acc < 2; ++acc)
         for (int e = 0; e < 2; ++e)
             if (ctx->occ_attr[acc][e][kAttrDefault] < 1 || ctx->occ_rep[acc][e][kRepDefault] < 1)
@@ -329,6 +337,7 @@ int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, 
     P.o_coords = cv.take(((size_t)P.gxp + P.ny + P.nz) * sizeof(float));
     P.o_parta = cv.take((size_t)part_units * kTile * sizeof(dacc4));
     P.o_partr = cv.take((size_t)part_units * kTile * sizeof(dacc4));
+    P.o_racc = cv.take((size_t)N * 3 * sizeof(unsigned long long));
     P.o_eblocks = cv.take((size_t)energy_blocks(N) * sizeof(double2));
     P.o_g64 = need_g64 ? cv.take((size_t)N * 3 * sizeof(double)) : 0;
     P.end = cv.off;
@@ -437,7 +446,8 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     RepArgs ra;
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
-    const bool need_a = attr_choice_of(ctx, acc, P.gxp) < 0, need_r = ctx->rep_choice[acc] < 0;
+    const bool need_a = attr_choice_of(ctx, acc, P.gxp) < 0,
+               need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0;
     if (ctx->autotune && (need_a || need_r)) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(st, &cap));
@@ -455,7 +465,19 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         CK(launch_attraction(aa, acc, energy, P.va, st));
         ls.done();
     }
-    {
+    unsigned long long *racc = nullptr;
+    if (ctx->rep_symmetric) {
+        // every unordered pair once, exact fixed-point totals
+        racc = at<unsigned long long>(ctx, P.o_racc);
+        SymArgs sa;
+        sa.pos = pos; sa.N = P.N; sa.tiles = P.tiles;
+        sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[energy ? 1 : 0];
+        sa.acc = racc; sa.status = ctx->d_status;
+        LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
+        CK(cudaMemsetAsync(racc, 0, (size_t)P.N * (energy ? 1 : 3) * sizeof(unsigned long long), st));
+        CK(launch_repulsion_sym(sa, energy, st));
+        ls.done();
+    } else {
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
         CK(launch_repulsion(ra, acc, energy, P.vr, st));
         ls.done();
@@ -464,6 +486,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     cb.N = P.N; cb.part_a = aa.part; cb.part_r = ra.part; cb.spa = P.spa; cb.spr = P.spr;
     cb.G = G; cb.A = A; cb.R = R;
     cb.G64 = g64 ? at<double>(ctx, P.o_g64) : nullptr;
+    cb.racc = racc;
     cb.scale = scale;
     cb.scale_dev = scale_dev;
     cb.energy_blocks = at<double2>(ctx, P.o_eblocks);
@@ -610,6 +633,7 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
     const double target = (double)total / ((double)ctas * items_per_cta);
     b.traj.assign(B, EngineTraj());
     b.items.clear();
+    b.item_pairs.clear();
     int64_t part = 0;
     for (int t = 0; t < B; ++t) {
         EngineTraj &tr = b.traj[t];
@@ -638,12 +662,14 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
         for (int64_t tile = 0; tile < tr.tiles; ++tile) {
             int ia = 0, ir = 0;
             while (ia < ach || ir < rch) {
+                const double tgt = (double)std::min<int64_t>(kTile, N - tile * kTile);
                 if (ia < ach) {
                     EngineItem it;
                     it.kind = kItemAttraction; it.traj = t; it.tile = (int32_t)tile; it.slot = ia;
                     it.u0 = ia * rc;
                     it.u1 = (ia + 1) * rc < rows ? (ia + 1) * rc : rows;
                     b.items.push_back(it);
+                    b.item_pairs.push_back(tgt * (double)(it.u1 - it.u0) * nx);
                     ++ia;
                 }
                 if (ir < rch) {
@@ -653,11 +679,14 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
                     it.u0 = ir * sc;
                     it.u1 = (ir + 1) * sc < blocks ? (ir + 1) * sc : blocks;
                     b.items.push_back(it);
+                    b.item_pairs.push_back(tgt * (double)(std::min<int64_t>(it.u1 * kSrcBlock, N) -
+                                                          it.u0 * kSrcBlock));
                     ++ir;
                 }
             }
         }
     }
+    b.n_pair_items = (int64_t)b.items.size();
     for (int t = 0; t < B; ++t)
         for (int c = 0; c < b.traj[t].Nc; ++c) {
             EngineItem it;
@@ -695,24 +724,33 @@ int validate_batch(sparkling_ctx *ctx, int32_t B, const int64_t *off, const void
     return SPARKLING_OK;
 }
 
-// Device work of one batched step on `st`: reset the counters, pack the
-// samples and the densities, run the engine.
-int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_grid *grids,
-                      int acc, cudaStream_t st)
+// Pack the samples of all trajectories and every density grid.
+int batch_pack(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_grid *grids,
+               cudaStream_t st)
 {
     sparkling_ctx::Batch &b = ctx->batch;
     const int B = b.B;
-    const int64_t Ntot = b.off[B];
-    CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0, (size_t)(B + 1) * sizeof(unsigned int), st));
-    CK(launch_pack_positions(K, K_dtype, Ntot, at<float4>(ctx, b.o_pos), ctx->d_status, ctx->sms, st));
+    CK(launch_pack_positions(K, K_dtype, b.off[B], at<float4>(ctx, b.o_pos), ctx->d_status,
+                             ctx->sms, st));
     for (int t = 0; t < B; ++t)
         CK(launch_pack_grid(grids[t].rho, grids[t].n[0], grids[t].n[1], grids[t].n[2],
                             b.traj[t].gxp, grids[t].lo, grids[t].hi, at<float>(ctx, b.o_rho[t]),
                             at<float>(ctx, b.o_coords[t]), ctx->d_status, ctx->sms, st));
+    return SPARKLING_OK;
+}
+
+// Reset the counters and run the first n_items items of the work list with
+// engine tile shape `variant`.
+int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant, int64_t n_items,
+                 cudaStream_t st)
+{
+    sparkling_ctx::Batch &b = ctx->batch;
+    CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0, (size_t)(b.B + 1) * sizeof(unsigned int),
+                       st));
     EngineArgs e;
     e.traj = at<EngineTraj>(ctx, b.o_traj);
     e.items = at<EngineItem>(ctx, b.o_items);
-    e.n_items = (int32_t)b.items.size();
+    e.n_items = (int32_t)n_items;
     e.proj_in_smem = b.proj_in_smem ? 1 : 0;
     e.pos = at<float4>(ctx, b.o_pos);
     e.K = K;
@@ -721,7 +759,54 @@ int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_
     e.done = e.queue + 1;
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
     e.status = ctx->d_status;
-    CK(launch_engine(e, acc, K_dtype, b.ctas, st));
+    const int ctas = ctx->sms * engine_ctas_per_sm(acc, K_dtype, variant);
+    CK(launch_engine(e, acc, K_dtype, variant, std::min(ctas, b.ctas), st));
+    return SPARKLING_OK;
+}
+
+// Device work of one batched step on `st`: pack, then the whole work list.
+int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_grid *grids,
+                      int acc, int variant, cudaStream_t st)
+{
+    int s;
+    if ((s = batch_pack(ctx, K, K_dtype, grids, st))) return s;
+    return batch_engine(ctx, K, K_dtype, acc, variant, (int64_t)ctx->batch.items.size(), st);
+}
+
+// Engine autotuner: time each tile shape on a prefix of the pair items (about
+// 1.5e11 pairs; pair items only write partial slots, which the real step
+// overwrites, so K is untouched) after one warm-up, and keep the fastest.
+int tune_engine(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_grid *grids, int acc,
+                cudaStream_t st)
+{
+    sparkling_ctx::Batch &b = ctx->batch;
+    int s;
+    if ((s = batch_pack(ctx, K, K_dtype, grids, st))) return s;
+    int64_t n = 0;
+    double pairs = 0.0;
+    while (n < b.n_pair_items && pairs < 1.5e11) pairs += b.item_pairs[n++];
+    cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+    int best = 0;
+    double best_rate = 0.0;
+    for (int v = 0; v < kEngineVariants; ++v) {
+        if (engine_ctas_per_sm(acc, K_dtype, v) < 1) { cudaGetLastError(); continue; }
+        if ((s = batch_engine(ctx, K, K_dtype, acc, v, n, st))) return s;
+        CK(cudaEventRecord(e0, st));
+        if ((s = batch_engine(ctx, K, K_dtype, acc, v, n, st))) return s;
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
+        char line[160];
+        snprintf(line, sizeof line, "engine threads=%d: %.4g pairs/s (%lld pair items)\n",
+                 engine_variant_threads(v), rate, (long long)n);
+        ctx->tune_log += line;
+        if (rate > best_rate) { best_rate = rate; best = v; }
+    }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    ctx->engine_choice[acc][K_dtype] = best;
     return SPARKLING_OK;
 }
 
@@ -911,12 +996,11 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     std::vector<int32_t> dims;
     for (int t = 0; t < B; ++t)
         for (int a = 0; a < 3; ++a) dims.push_back(grids[t].n[a]);
-    const int occ = engine_ctas_per_sm(acc, K_dtype);
-    if (occ < 1) {
-        cudaGetLastError();
-        return fail(ctx, SPARKLING_E_CUDA, "engine kernel cannot be resident");
-    }
-    const int ctas = ctx->sms * occ;
+    int occ = 0;
+    for (int v = 0; v < kEngineVariants; ++v) occ = std::max(occ, engine_ctas_per_sm(acc, K_dtype, v));
+    cudaGetLastError();
+    if (occ < 1) return fail(ctx, SPARKLING_E_CUDA, "engine kernel cannot be resident");
+    const int ctas = ctx->sms * occ;   // the largest wave of any engine shape
     const bool same = b.valid && b.B == B && b.Ns == Ns && b.acc == acc && b.dtype == K_dtype &&
                       b.ctas == ctas && b.items_per_cta == ctx->items_per_cta && b.off == off &&
                       b.dims == dims;
@@ -977,16 +1061,20 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     CK(cudaMemcpyAsync(at<EngineTraj>(ctx, b.o_traj), ctx->h_traj, (size_t)B * sizeof(EngineTraj),
                        cudaMemcpyHostToDevice, st));
 
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (ctx->autotune && ctx->engine_choice[acc][K_dtype] < 0 && cap == cudaStreamCaptureStatusNone)
+        if ((s = tune_engine(ctx, K, K_dtype, grids, acc, st))) return s;
+    const int variant = ctx->engine_choice[acc][K_dtype] < 0 ? 0 : ctx->engine_choice[acc][K_dtype];
+
     // Graph replay when asked for and the call matches the captured one.
     std::vector<const void *> key;
     key.push_back(K);
     key.push_back(ctx->ws);
     for (int t = 0; t < B; ++t) key.push_back(grids[t].rho);
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CK(cudaStreamIsCapturing(st, &cap));
     const bool use_graph = (flags & SPARKLING_BATCH_GRAPH) && cap == cudaStreamCaptureStatusNone;
     LaunchScope ls(ctx, SPARKLING_KERNEL_ENGINE, st);
-    if (use_graph && b.exec && b.graph_key == key) {
+    if (use_graph && b.exec && b.graph_key == key && b.graph_variant == variant) {
         CK(cudaGraphLaunch(b.exec, st));
     } else if (use_graph && b.eager_calls > 0) {
         // Capture (which records without executing) on a private stream --
@@ -997,7 +1085,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
             CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        const int w = batch_device_work(ctx, K, K_dtype, grids, acc, ctx->cap_stream);
+        const int w = batch_device_work(ctx, K, K_dtype, grids, acc, variant, ctx->cap_stream);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (w) { if (g) cudaGraphDestroy(g); return w; }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
@@ -1005,9 +1093,10 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         cudaGraphDestroy(g);
         if (e != cudaSuccess) { b.exec = nullptr; return cuda_fail(ctx, e, "cudaGraphInstantiate"); }
         b.graph_key = key;
+        b.graph_variant = variant;
         CK(cudaGraphLaunch(b.exec, st));
     } else {
-        if ((s = batch_device_work(ctx, K, K_dtype, grids, acc, st))) return s;
+        if ((s = batch_device_work(ctx, K, K_dtype, grids, acc, variant, st))) return s;
         ++b.eager_calls;
     }
     ls.done((int)b.kernels_per_step);
@@ -1108,6 +1197,7 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable)
     if (enable < 0) {   // forget the choices made so far
         ctx->attr_choice.clear();
         ctx->rep_choice[0] = ctx->rep_choice[1] = -1;
+        for (auto &row : ctx->engine_choice) row[0] = row[1] = -1;
         ctx->tune_log.clear();
         ctx->autotune = true;
     }

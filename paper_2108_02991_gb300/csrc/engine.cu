@@ -108,8 +108,10 @@ __device__ __forceinline__ RepArgs rep_args(const EngineTraj &t, const EngineArg
     return r;
 }
 
-template <int ACC, typename KT>
-__global__ void __launch_bounds__(kThreads, 3) engine_kernel(const EngineArgs e)
+// NT threads per CTA: 256 (4 targets per thread, repulsion unroll 4, three
+// CTAs per SM) or 512 (2 targets per thread, unroll 2, two CTAs per SM).
+template <int ACC, typename KT, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const EngineArgs e)
 {
     extern __shared__ __align__(128) unsigned char esm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(esm);
@@ -136,13 +138,13 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(const EngineArgs e)
         const EngineTraj &tr = e.traj[item.traj];
         if (item.kind == kItemAttraction) {
             const AttrArgs a = attr_args(tr, e);
-            if (!attraction_segment<ACC, false, kThreads>(a, item.tile, item.u0, item.u1, item.slot, stage,
+            if (!attraction_segment<ACC, false, NT>(a, item.tile, item.u0, item.u1, item.slot, stage,
                                                 bars, accbase, consumed))
                 return;
             mark_done(e.done + item.traj);
         } else if (item.kind == kItemRepulsion) {
             const RepArgs r = rep_args(tr, e);
-            if (!repulsion_segment<ACC, false, kThreads, 2>(r, item.tile, item.u0, item.u1, item.slot,
+            if (!repulsion_segment<ACC, false, NT, (NT >= 512 ? 2 : 4)>(r, item.tile, item.u0, item.u1, item.slot,
                                                reinterpret_cast<float4 *>(stage), bars, accbase,
                                                consumed))
                 return;
@@ -193,13 +195,19 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(const EngineArgs e)
     }
 }
 
-template <int ACC, typename KT>
-void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT>); }
+template <int ACC, typename KT, int NT>
+void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT, NT>); }
 
-void *pick_engine(int acc, int dtype)
+template <int NT>
+void *pick_engine_nt(int acc, int dtype)
 {
-    if (acc == 0) return dtype == 0 ? engine_fn<0, float>() : engine_fn<0, double>();
-    return dtype == 0 ? engine_fn<1, float>() : engine_fn<1, double>();
+    if (acc == 0) return dtype == 0 ? engine_fn<0, float, NT>() : engine_fn<0, double, NT>();
+    return dtype == 0 ? engine_fn<1, float, NT>() : engine_fn<1, double, NT>();
+}
+
+void *pick_engine(int acc, int dtype, int variant)
+{
+    return variant == 1 ? pick_engine_nt<512>(acc, dtype) : pick_engine_nt<256>(acc, dtype);
 }
 
 } // namespace
@@ -208,24 +216,29 @@ size_t engine_smem_bytes() { return kHeadBytes + kUnionBytes; }
 
 size_t engine_proj_smem_limit() { return kUnionBytes; }
 
-int engine_ctas_per_sm(int acc, int dtype)
+int engine_variant_threads(int v) { return v == 1 ? 512 : 256; }
+
+int engine_ctas_per_sm(int acc, int dtype, int variant)
 {
-    void *fn = pick_engine(acc, dtype);
+    void *fn = pick_engine(acc, dtype, variant);
     const size_t smem = engine_smem_bytes();
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, engine_variant_threads(variant),
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int ctas, cudaStream_t st)
+cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int variant, int ctas,
+                          cudaStream_t st)
 {
-    void *fn = pick_engine(acc, dtype);
+    void *fn = pick_engine(acc, dtype, variant);
     void *args[] = {const_cast<EngineArgs *>(&e)};
-    return cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(kThreads), args, engine_smem_bytes(), st);
+    return cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(engine_variant_threads(variant)), args,
+                            engine_smem_bytes(), st);
 }
 
 } // namespace sparkling

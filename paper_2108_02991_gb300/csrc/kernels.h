@@ -1,6 +1,7 @@
 // Internal interface between the C-ABI layer (api.cu) and the kernels
 // (pairs.cu, project.cu).  Not installed; not part of the ABI.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -63,6 +64,43 @@ inline Split make_split(int64_t tiles, int64_t per_tile, int64_t max_ctas)
     return s;
 }
 
+// Upper triangle of tile pairs (I, J), 0 <= I <= J < T, numbered row by row:
+// row I holds T - I pairs and starts at tri_row_start(I, T).
+__host__ __device__ inline int64_t tri_row_start(int64_t I, int64_t T)
+{
+    return I * T - I * (I - 1) / 2;
+}
+
+__host__ __device__ inline int64_t tri_count(int64_t T) { return T * (T + 1) / 2; }
+
+// (I, J) of pair number u (0 <= u < tri_count(T)).
+__host__ __device__ inline void tri_pair(int64_t u, int64_t T, int64_t &I, int64_t &J)
+{
+    const double b = 2.0 * (double)T + 1.0;
+    double d = b * b - 8.0 * (double)u;
+    d = d > 0.0 ? d : 0.0;
+    int64_t i = (int64_t)((b - sqrt(d)) * 0.5);
+    if (i < 0) i = 0;
+    if (i > T - 1) i = T - 1;
+    while (i + 1 <= T - 1 && tri_row_start(i + 1, T) <= u) ++i;
+    while (i > 0 && tri_row_start(i, T) > u) --i;
+    I = i;
+    J = i + (u - tri_row_start(i, T));
+}
+
+// Fixed-point scale of the symmetric repulsion's integer accumulators: a sum
+// is kept as round(x * 2^32) in an int64 (exact, order-independent addition).
+constexpr double kFixScale = 4294967296.0;
+
+struct SymArgs {
+    const float4 *pos;          // packed samples [N]
+    int64_t N;
+    int64_t tiles;              // ceil(N / kTile)
+    int64_t ctas;               // persistent CTAs; tri_count(tiles) units split evenly
+    unsigned long long *acc;    // [N][NV] fixed-point sums (zeroed before the launch)
+    int *status;
+};
+
 struct AttrArgs {
     const float4 *tgt;    // packed targets (x, y, z, 0) [N]
     int64_t N;
@@ -92,6 +130,7 @@ struct CombineArgs {
     Split spa, spr;
     void *G, *A, *R;      // outputs [N][3] (A, R may be null)
     double *G64;          // optional FP64 copy of G [N][3]
+    const unsigned long long *racc;   // symmetric repulsion sums [N][NV] (replaces part_r)
     double scale;         // G, A, R are multiplied by scale * (*scale_dev if set)
     const double *scale_dev;
     double2 *energy_blocks;  // energy mode: per-block (sum ea, sum er)
@@ -121,6 +160,10 @@ size_t repulsion_smem_bytes();
 int repulsion_ctas_per_sm(int acc, bool energy, int variant);
 cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st);
+// Symmetric repulsion (repulsion_sym.cu): every unordered pair once.
+size_t repulsion_sym_smem_bytes();
+int repulsion_sym_ctas_per_sm(bool energy);
+cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, cudaStream_t st);
 int energy_blocks(int64_t N);
 cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream_t st);
 
@@ -191,7 +234,10 @@ struct EngineArgs {
 
 size_t engine_smem_bytes();
 size_t engine_proj_smem_limit();     // largest 18*Ns*8 that fits the shared-memory union
-int engine_ctas_per_sm(int acc, int dtype);
-cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int ctas, cudaStream_t st);
+constexpr int kEngineVariants = 2;    // threads 256 (repulsion unroll 4) / 512 (unroll 2)
+int engine_variant_threads(int v);
+int engine_ctas_per_sm(int acc, int dtype, int variant);
+cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int variant, int ctas,
+                          cudaStream_t st);
 
 } // namespace sparkling

@@ -124,7 +124,15 @@ __global__ void combine_kernel(const CombineArgs c)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.N;
          i += (int64_t)gridDim.x * blockDim.x) {
         dacc4 a = sum_slots(c.part_a, c.spa, i);
-        const dacc4 r = sum_slots(c.part_r, c.spr, i);
+        dacc4 r;
+        if (c.racc) {
+            r.x = (double)(long long)c.racc[3 * i] / kFixScale;
+            r.y = (double)(long long)c.racc[3 * i + 1] / kFixScale;
+            r.z = (double)(long long)c.racc[3 * i + 2] / kFixScale;
+            r.w = 0.0;
+        } else {
+            r = sum_slots(c.part_r, c.spr, i);
+        }
         double rx = r.x * invN, ry = r.y * invN, rz = r.z * invN;
         double gx = a.x - rx, gy = a.y - ry, gz = a.z - rz;
         if (sc != 1.0) {
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_block_kernel(const Comb
         const int64_t i = (int64_t)blockIdx.x * kEnergyBlock + k * kEnergyThreads + threadIdx.x;
         if (i < c.N) {
             ea += sum_slots(c.part_a, c.spa, i).w;
-            er += sum_slots(c.part_r, c.spr, i).w;
+            er += c.racc ? (double)(long long)c.racc[i] / kFixScale : sum_slots(c.part_r, c.spr, i).w;
         }
     }
     const double2 s = block_sum2(ea, er);

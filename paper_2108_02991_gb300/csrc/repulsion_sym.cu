@@ -1,0 +1,303 @@
+// Symmetric repulsion: R_i = (1/N) sum_j (k_i - k_j)/|k_i - k_j| (paper
+// eq. Fr_grad with H' = 1) with every unordered pair evaluated once.  The
+// pair term is odd in (i, j), so the term computed for (i, j) is added to
+// sample i and subtracted from sample j: half the reciprocal square roots
+// and ~35% fewer instructions per directed pair than the directed kernel.
+//
+// Work: the upper triangle of tile pairs (I, J), I <= J, tiles of 1024
+// samples, split evenly over one wave of persistent CTAs (contiguous runs of
+// a row share the target tile I).  In a CTA, warp w holds 128 targets of
+// tile I (4 per lane) and, in round r, the 128 sources of chunk (w + r) mod 8
+// of tile J (4 per lane, staged by a TMA bulk copy).  The sources and their
+// accumulators rotate one lane per step through the 32 lanes, so after 32
+// steps every (target, source) pair of the two chunks has met once and each
+// source is back home; its accumulator is then added to a shared-memory
+// j-accumulator, which no other warp touches in that round.  A diagonal pair
+// (I, I) is evaluated directed (targets only).
+//
+// Totals are kept as fixed-point integers (x * 2^32 in int64) and added with
+// 64-bit atomics: integer addition is exact and order-independent, so the
+// result does not depend on the schedule.  The per-item sums converted to
+// fixed point are FP32 sums of <= 1024 unit-vector components.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "kernels.h"
+#include "ptx.cuh"
+
+namespace sparkling {
+
+namespace {
+
+constexpr int kSymThreads = 256;
+constexpr int kSymWarps = kSymThreads / 32;
+constexpr int kSymT = 4;                       // targets per lane
+constexpr int kSymS = 4;                       // sources per lane per chunk
+constexpr int kSymChunk = 32 * kSymS;          // 128 sources per chunk
+constexpr int kSymStages = 2;                  // J tiles in flight
+static_assert(kSymWarps * 32 * kSymT == kTile, "a CTA holds one tile of targets");
+static_assert(kSymWarps * kSymChunk == kTile, "a tile is one chunk per warp");
+
+// Shared memory: mbarriers | J-tile stages | FP32 j-accumulator [NV][1024] |
+// per-thread int64 i-accumulators [T*NV][256].
+constexpr size_t kSymHead = 64;
+constexpr size_t kSymStageBytes = (size_t)kTile * sizeof(float4);
+constexpr size_t kSymJaccBytes = 3 * kTile * sizeof(float);
+constexpr size_t kSymIaccBytes = (size_t)kSymT * 3 * kSymThreads * sizeof(long long);
+
+__device__ __forceinline__ long long to_fix(float x)
+{
+    return __float2ll_rn(x * 4294967296.0f);
+}
+
+__device__ __forceinline__ void add_fix(unsigned long long *p, long long v)
+{
+    if (v != 0) atomicAdd(p, (unsigned long long)v);
+}
+
+// One off-diagonal item: the thread's kSymT targets against tile J (in src,
+// jvalid valid sources).  Target sums go to ai (registers), source sums to
+// jacc ([NV][kTile], shared).  RAGGED: the last tile is partial; tm/sm mask
+// the missing targets/sources to zero.
+template <bool ENERGY, bool RAGGED>
+__device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const float *tx,
+                                         const float *ty, const float *tz, const float *tm,
+                                         float (*ai)[3], float *jacc)
+{
+    constexpr int T = kSymT, S = kSymS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int from = (lane + 1) & 31;
+    for (int r = 0; r < kSymWarps; ++r) {
+        const int c = (warp + r) & (kSymWarps - 1);
+        float sx[S], sy[S], sz[S], sm[S], bx[S], by[S], bz[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int j = c * kSymChunk + s * 32 + lane;
+            const bool ok = !RAGGED || j < jvalid;
+            // a missing source (stale shared memory, possibly NaN) becomes a
+            // finite point whose terms the zero mask then removes
+            const float4 q = ok ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sx[s] = q.x; sy[s] = q.y; sz[s] = q.z;
+            sm[s] = ok ? 1.f : 0.f;
+            bx[s] = 0.f; by[s] = 0.f; bz[s] = 0.f;
+        }
+        for (int step = 0; step < 32; ++step) {
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const float dx = tx[t] - sx[s], dy = ty[t] - sy[s], dz = tz[t] - sz[s];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
+                    float ri = rsqrt_sfu(r2);
+                    if (RAGGED) ri *= tm[t] * sm[s];
+                    if (ENERGY) {
+                        const float e = r2 * ri;          // |d|, counted for both samples
+                        ai[t][0] += e;
+                        bx[s] += e;
+                    } else {
+                        ai[t][0] = fmaf(dx, ri, ai[t][0]);
+                        ai[t][1] = fmaf(dy, ri, ai[t][1]);
+                        ai[t][2] = fmaf(dz, ri, ai[t][2]);
+                        bx[s] = fmaf(-dx, ri, bx[s]);
+                        by[s] = fmaf(-dy, ri, by[s]);
+                        bz[s] = fmaf(-dz, ri, bz[s]);
+                    }
+                }
+            }
+            // the sources and their sums move one lane down
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                sx[s] = __shfl_sync(0xffffffffu, sx[s], from);
+                sy[s] = __shfl_sync(0xffffffffu, sy[s], from);
+                sz[s] = __shfl_sync(0xffffffffu, sz[s], from);
+                if (RAGGED) sm[s] = __shfl_sync(0xffffffffu, sm[s], from);
+                bx[s] = __shfl_sync(0xffffffffu, bx[s], from);
+                if (!ENERGY) {
+                    by[s] = __shfl_sync(0xffffffffu, by[s], from);
+                    bz[s] = __shfl_sync(0xffffffffu, bz[s], from);
+                }
+            }
+        }
+        // 32 steps later every source is back in its lane: this warp alone
+        // owns chunk c in round r
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int j = c * kSymChunk + s * 32 + lane;
+            jacc[j] += bx[s];
+            if (!ENERGY) {
+                jacc[kTile + j] += by[s];
+                jacc[2 * kTile + j] += bz[s];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// A diagonal item (I, I): the thread's targets against every source of the
+// tile, directed (each ordered pair once, target side only; the zero-distance
+// self term contributes nothing).
+template <bool ENERGY>
+__device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const float *tx,
+                                          const float *ty, const float *tz, float (*ai)[3])
+{
+    constexpr int T = kSymT;
+#pragma unroll 2
+    for (int j = 0; j < jvalid; ++j) {
+        const float4 q = src[j];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float dx = tx[t] - q.x, dy = ty[t] - q.y, dz = tz[t] - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
+            const float ri = rsqrt_sfu(r2);
+            if (ENERGY) {
+                ai[t][0] = fmaf(r2, ri, ai[t][0]);
+            } else {
+                ai[t][0] = fmaf(dx, ri, ai[t][0]);
+                ai[t][1] = fmaf(dy, ri, ai[t][1]);
+                ai[t][2] = fmaf(dz, ri, ai[t][2]);
+            }
+        }
+    }
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
+{
+    constexpr int T = kSymT;
+    constexpr int NV = ENERGY ? 1 : 3;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float4 *stage = reinterpret_cast<float4 *>(smem + kSymHead);
+    float *jacc = reinterpret_cast<float *>(smem + kSymHead + kSymStages * kSymStageBytes);
+    long long *iacc = reinterpret_cast<long long *>(smem + kSymHead + kSymStages * kSymStageBytes +
+                                                    kSymJaccBytes);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t U = tri_count(a.tiles);
+    const int64_t u0 = U * blockIdx.x / a.ctas, u1 = U * (blockIdx.x + 1) / a.ctas;
+    if (u0 >= u1) return;
+    if (tid == 0) {
+        for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int nlast = (int)(a.N - (a.tiles - 1) * kTile);
+    auto count_of = [&](int64_t J) { return J == a.tiles - 1 ? nlast : kTile; };
+    auto advance = [&](int64_t &I, int64_t &J) {
+        if (++J == a.tiles) { ++I; J = I; }
+    };
+    auto issue = [&](uint32_t g, int64_t J) {
+        bulk_load(stage + (g % kSymStages) * kTile, a.pos + J * kTile,
+                  (uint32_t)(count_of(J) * sizeof(float4)), &bars[g % kSymStages]);
+    };
+    const uint32_t n = (uint32_t)(u1 - u0);
+    int64_t I, J, qI, qJ;
+    tri_pair(u0, a.tiles, I, J);
+    qI = I; qJ = J;                      // cursor of the next tile to prefetch
+    for (uint32_t g = 0; g < n && g < (uint32_t)kSymStages; ++g) {
+        if (tid == 0) issue(g, qJ);
+        advance(qI, qJ);
+    }
+    int64_t curI = -1;
+    float tx[T], ty[T], tz[T], tm[T];
+    // the thread's targets of tile curI: l = warp*128 + t*32 + lane
+    auto flush_i = [&]() {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = curI * kTile + warp * kSymChunk + t * 32 + lane;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                long long &x = iacc[(t * NV + v) * kSymThreads + tid];
+                if (i < a.N) add_fix(&a.acc[i * NV + v], x);
+                x = 0;
+            }
+        }
+    };
+    for (uint32_t g = 0; g < n; ++g) {
+        if (I != curI) {
+            if (curI >= 0) flush_i();
+            curI = I;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int64_t i = I * kTile + warp * kSymChunk + t * 32 + lane;
+                const bool ok = i < a.N;
+                const float4 p = ok ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                tx[t] = p.x; ty[t] = p.y; tz[t] = p.z; tm[t] = ok ? 1.f : 0.f;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * kSymThreads + tid] = 0;
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bars[g % kSymStages], (g / kSymStages) & 1, a.status);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0)
+                for (uint32_t h = g; h < n && h < g + kSymStages; ++h)
+                    mbar_wait_bounded(&bars[h % kSymStages], (h / kSymStages) & 1, a.status);
+            __syncthreads();
+            return;
+        }
+        const float4 *src = stage + (g % kSymStages) * kTile;
+        const int jvalid = count_of(J);
+        float ai[T][3];
+#pragma unroll
+        for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
+        if (I == J) {
+            diag_item<ENERGY>(src, jvalid, tx, ty, tz, ai);
+        } else {
+            for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
+            __syncthreads();
+            if (jvalid < kTile)
+                sym_item<ENERGY, true>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+            else
+                sym_item<ENERGY, false>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+            for (int l = tid; l < jvalid; l += kSymThreads)
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    add_fix(&a.acc[(J * kTile + l) * NV + v], to_fix(jacc[v * kTile + l]));
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * kSymThreads + tid] += to_fix(ai[t][v]);
+        __syncthreads();   // stage g consumed, jacc flushed
+        if (g + kSymStages < n) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                issue(g + kSymStages, qJ);
+            }
+            advance(qI, qJ);
+        }
+        advance(I, J);
+    }
+    flush_i();
+}
+
+template <bool E>
+void *sym_fn() { return reinterpret_cast<void *>(repulsion_sym_kernel<E>); }
+
+} // namespace
+
+size_t repulsion_sym_smem_bytes()
+{
+    return kSymHead + kSymStages * kSymStageBytes + kSymJaccBytes + kSymIaccBytes;
+}
+
+int repulsion_sym_ctas_per_sm(bool energy)
+{
+    void *fn = energy ? sym_fn<true>() : sym_fn<false>();
+    const size_t smem = repulsion_sym_smem_bytes();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kSymThreads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, cudaStream_t st)
+{
+    void *fn = energy ? sym_fn<true>() : sym_fn<false>();
+    void *args[] = {const_cast<SymArgs *>(&a)};
+    return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(kSymThreads), args,
+                            repulsion_sym_smem_bytes(), st);
+}
+
+} // namespace sparkling

@@ -189,3 +189,50 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(sp, "_lib_handle", None)
     with pytest.raises(ImportError):
         sp.lib()
+
+
+@needs_nvcc
+def test_triangle_pair_numbering(tmp_path):
+    """Tile pairs (I, J), I <= J, numbered row by row: tri_pair inverts the
+    numbering exactly (every pair of small triangles, sampled large ones)."""
+    src = tmp_path / "tri.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include "kernels.h"
+using namespace sparkling;
+int main() {
+  long bad = 0, checked = 0;
+  for (long T = 1; T <= 60; ++T) {
+    long u = 0;
+    for (long I = 0; I < T; ++I)
+      for (long J = I; J < T; ++J, ++u) {
+        int64_t i, j; tri_pair(u, T, i, j);
+        if (i != I || j != J) ++bad;
+        ++checked;
+      }
+    if (u != tri_count(T)) ++bad;
+  }
+  const long big[] = {1024, 10240, 100000, 2097151};
+  for (long T : big) {
+    const long U = tri_count(T);
+    for (long k = 0; k < 200000; ++k) {
+      const long u = (long)((double)k / 200000 * U) + (k % 7);
+      if (u >= U) continue;
+      int64_t i, j; tri_pair(u, T, i, j);
+      if (i < 0 || j < i || j >= T || tri_row_start(i, T) + (j - i) != u) ++bad;
+      ++checked;
+    }
+    int64_t i, j; tri_pair(U - 1, T, i, j);
+    if (i != T - 1 || j != T - 1) ++bad;
+  }
+  std::printf("%ld %ld\n", checked, bad);
+  return bad != 0;
+}
+''')
+    exe = tmp_path / "tri"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I",
+                    os.path.join(ROOT, "paper_2108_02991_gb300", "csrc"), "-I",
+                    "/usr/local/cuda/include", str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    checked, bad = map(int, r.stdout.split())
+    assert checked > 500000 and bad == 0
