@@ -51,7 +51,8 @@ struct sparkling_ctx {
     std::vector<std::pair<int64_t, int>> attr_choice;   // key acc * 2^20 + gxp
     int rep_choice[2] = {-1, -1};
     bool rep_symmetric = true;     // repulsion: symmetric kernel (else the directed shapes)
-    int occ_sym[2] = {0, 0};
+    int occ_sym[2][kSymVariants] = {};
+    int sym_choice = -1;           // sources per lane of the symmetric kernel (variant)
     std::string tune_log;
     // batched step: cached work list, workspace layout and CUDA graph
     struct Batch {
@@ -278,9 +279,13 @@ int ensure_occupancy(sparkling_ctx *ctx)
             for (int v = 0; v < kRepVariants; ++v)
                 ctx->occ_rep[acc][e][v] = repulsion_ctas_per_sm(acc, e != 0, v);
         }
-    for (int e = 0; e < 2; ++e) ctx->occ_sym[e] = repulsion_sym_ctas_per_sm(e != 0);
+    for (int e = 0; e < 2; ++e)
+        for (int v = 0; v < kSymVariants; ++v)
+            ctx->occ_sym[e][v] = repulsion_sym_ctas_per_sm(e != 0, v);
     cudaGetLastError();
-    if (ctx->occ_sym[0] < 1 || ctx->occ_sym[1] < 1) ctx->rep_symmetric = false;
+    for (int e = 0; e < 2; ++e)
+        for (int v = 0; v < kSymVariants; ++v)
+            if (ctx->occ_sym[e][v] < 1) ctx->rep_symmetric = false;
     for (int acc = 0; acc < 2; ++acc)
         for (int e = 0; e < 2; ++e)
             if (ctx->occ_attr[acc][e][kAttrDefault] < 1 || ctx->occ_rep[acc][e][kRepDefault] < 1)
@@ -356,7 +361,7 @@ template <typename T> T *at(sparkling_ctx *ctx, size_t off)
 // Runs once per key (acc and padded row length for the attraction, acc for
 // the repulsion) and synchronises the stream.
 int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra, bool do_attr,
-               bool do_rep, cudaStream_t st)
+               bool do_rep, bool do_sym, unsigned long long *racc, cudaStream_t st)
 {
     cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
     const int64_t rows = (int64_t)P.ny * P.nz;
@@ -413,6 +418,27 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
         }
         ctx->rep_choice[acc] = best;
     }
+    if (do_sym) {
+        // a sub-triangle of about 1e11 directed pairs (the first tt tiles)
+        int64_t tt = (int64_t)(std::sqrt(budget) / kTile + 0.5);
+        tt = std::max<int64_t>(1, std::min<int64_t>(tt, P.tiles));
+        SymArgs sa;
+        sa.pos = ra.pos; sa.N = std::min<int64_t>(P.N, tt * kTile); sa.tiles = tt;
+        sa.acc = racc; sa.status = ctx->d_status;
+        int best = 0;
+        double best_rate = 0.0;
+        for (int v = 0; v < kSymVariants; ++v) {
+            sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[0][v];
+            const double ms = timed([&] { return launch_repulsion_sym(sa, false, v, st); });
+            const double pairs = (double)sa.N * (double)(sa.N - 1);
+            const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
+            snprintf(line, sizeof line, "repulsion symmetric sources/lane=%d: %.4g pairs/s\n",
+                     sym_variant_sources(v), rate);
+            ctx->tune_log += line;
+            if (rate > best_rate) { best_rate = rate; best = v; }
+        }
+        ctx->sym_choice = best;
+    }
     ctx->pool.push_back(e0);
     ctx->pool.push_back(e1);
     cudaError_t err = cudaGetLastError();
@@ -447,12 +473,14 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
     const bool need_a = attr_choice_of(ctx, acc, P.gxp) < 0,
-               need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0;
-    if (ctx->autotune && (need_a || need_r)) {
+               need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
+               need_s = ctx->rep_symmetric && ctx->sym_choice < 0;
+    if (ctx->autotune && (need_a || need_r || need_s)) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(st, &cap));
         if (cap == cudaStreamCaptureStatusNone) {
-            int s = tune_pairs(ctx, P, acc, aa, ra, need_a, need_r, st);
+            int s = tune_pairs(ctx, P, acc, aa, ra, need_a, need_r, need_s,
+                               at<unsigned long long>(ctx, P.o_racc), st);
             if (s) return s;
             const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[acc];
             set_splits(ctx, P, acc, energy, va < 0 ? kAttrDefault : va, vr < 0 ? kRepDefault : vr);
@@ -471,11 +499,12 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         racc = at<unsigned long long>(ctx, P.o_racc);
         SymArgs sa;
         sa.pos = pos; sa.N = P.N; sa.tiles = P.tiles;
-        sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[energy ? 1 : 0];
+        const int sv = ctx->sym_choice < 0 ? 0 : ctx->sym_choice;
+        sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[energy ? 1 : 0][sv];
         sa.acc = racc; sa.status = ctx->d_status;
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
         CK(cudaMemsetAsync(racc, 0, (size_t)P.N * (energy ? 1 : 3) * sizeof(unsigned long long), st));
-        CK(launch_repulsion_sym(sa, energy, st));
+        CK(launch_repulsion_sym(sa, energy, sv, st));
         ls.done();
     } else {
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
@@ -1198,6 +1227,7 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable)
         ctx->attr_choice.clear();
         ctx->rep_choice[0] = ctx->rep_choice[1] = -1;
         for (auto &row : ctx->engine_choice) row[0] = row[1] = -1;
+        ctx->sym_choice = -1;
         ctx->tune_log.clear();
         ctx->autotune = true;
     }
@@ -1223,6 +1253,12 @@ SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, i
                      rep_variant_unroll(ctx->rep_choice[acc]));
             r += line;
         }
+    if (ctx->sym_choice >= 0) {
+        char line[128];
+        snprintf(line, sizeof line, "chosen repulsion symmetric: sources/lane=%d\n",
+                 sym_variant_sources(ctx->sym_choice));
+        r += line;
+    }
     const size_t n = std::min<size_t>(r.size(), (size_t)len - 1);
     std::memcpy(buf, r.data(), n);
     buf[n] = 0;

@@ -161,9 +161,11 @@ int repulsion_ctas_per_sm(int acc, bool energy, int variant);
 cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st);
 // Symmetric repulsion (repulsion_sym.cu): every unordered pair once.
+constexpr int kSymVariants = 2;       // sources per lane 2 / 4
+int sym_variant_sources(int v);
 size_t repulsion_sym_smem_bytes();
-int repulsion_sym_ctas_per_sm(bool energy);
-cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, cudaStream_t st);
+int repulsion_sym_ctas_per_sm(bool energy, int variant);
+cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st);
 int energy_blocks(int64_t N);
 cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream_t st);
 

@@ -32,11 +32,10 @@ namespace {
 constexpr int kSymThreads = 256;
 constexpr int kSymWarps = kSymThreads / 32;
 constexpr int kSymT = 4;                       // targets per lane
-constexpr int kSymS = 4;                       // sources per lane per chunk
-constexpr int kSymChunk = 32 * kSymS;          // 128 sources per chunk
 constexpr int kSymStages = 2;                  // J tiles in flight
 static_assert(kSymWarps * 32 * kSymT == kTile, "a CTA holds one tile of targets");
-static_assert(kSymWarps * kSymChunk == kTile, "a tile is one chunk per warp");
+// S sources per lane: a chunk is 32*S sources, a tile kTile/(32*S) chunks;
+// in round r warp w owns chunk (w + r) mod chunks.
 
 // Shared memory: mbarriers | J-tile stages | FP32 j-accumulator [NV][1024] |
 // per-thread int64 i-accumulators [T*NV][256].
@@ -59,16 +58,18 @@ __device__ __forceinline__ void add_fix(unsigned long long *p, long long v)
 // jvalid valid sources).  Target sums go to ai (registers), source sums to
 // jacc ([NV][kTile], shared).  RAGGED: the last tile is partial; tm/sm mask
 // the missing targets/sources to zero.
-template <bool ENERGY, bool RAGGED>
+template <bool ENERGY, bool RAGGED, int S>
 __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const float *tx,
                                          const float *ty, const float *tz, const float *tm,
                                          float (*ai)[3], float *jacc)
 {
-    constexpr int T = kSymT, S = kSymS;
+    constexpr int T = kSymT;
+    constexpr int kSymChunk = 32 * S, kChunks = kTile / kSymChunk;
+    static_assert(kChunks >= kSymWarps && (kChunks & (kChunks - 1)) == 0, "chunk count");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int from = (lane + 1) & 31;
-    for (int r = 0; r < kSymWarps; ++r) {
-        const int c = (warp + r) & (kSymWarps - 1);
+    for (int r = 0; r < kChunks; ++r) {
+        const int c = (warp + r) & (kChunks - 1);
         float sx[S], sy[S], sz[S], sm[S], bx[S], by[S], bz[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -160,7 +161,9 @@ __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const f
     }
 }
 
-template <bool ENERGY>
+constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
+
+template <bool ENERGY, int S>
 __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
 {
     constexpr int T = kSymT;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     auto flush_i = [&]() {
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const int64_t i = curI * kTile + warp * kSymChunk + t * 32 + lane;
+            const int64_t i = curI * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 long long &x = iacc[(t * NV + v) * kSymThreads + tid];
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
             curI = I;
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                const int64_t i = I * kTile + warp * kSymChunk + t * 32 + lane;
+                const int64_t i = I * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
                 const bool ok = i < a.N;
                 const float4 p = ok ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 tx[t] = p.x; ty[t] = p.y; tz[t] = p.z; tm[t] = ok ? 1.f : 0.f;
@@ -245,9 +248,9 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
             for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
             __syncthreads();
             if (jvalid < kTile)
-                sym_item<ENERGY, true>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, ai, jacc);
             else
-                sym_item<ENERGY, false>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, ai, jacc);
             for (int l = tid; l < jvalid; l += kSymThreads)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -271,18 +274,24 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
 }
 
 template <bool E>
-void *sym_fn() { return reinterpret_cast<void *>(repulsion_sym_kernel<E>); }
+void *sym_fn(int variant)
+{
+    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4>)
+                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2>);
+}
 
 } // namespace
+
+int sym_variant_sources(int v) { return v == 1 ? 4 : 2; }
 
 size_t repulsion_sym_smem_bytes()
 {
     return kSymHead + kSymStages * kSymStageBytes + kSymJaccBytes + kSymIaccBytes;
 }
 
-int repulsion_sym_ctas_per_sm(bool energy)
+int repulsion_sym_ctas_per_sm(bool energy, int variant)
 {
-    void *fn = energy ? sym_fn<true>() : sym_fn<false>();
+    void *fn = energy ? sym_fn<true>(variant) : sym_fn<false>(variant);
     const size_t smem = repulsion_sym_smem_bytes();
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
@@ -292,9 +301,9 @@ int repulsion_sym_ctas_per_sm(bool energy)
     return n;
 }
 
-cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, cudaStream_t st)
+cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st)
 {
-    void *fn = energy ? sym_fn<true>() : sym_fn<false>();
+    void *fn = energy ? sym_fn<true>(variant) : sym_fn<false>(variant);
     void *args[] = {const_cast<SymArgs *>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(kSymThreads), args,
                             repulsion_sym_smem_bytes(), st);
