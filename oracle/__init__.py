@@ -12,6 +12,8 @@ NumPy arrays.  See the C file for the definitions followed:
   repulsion_term, attraction_derivative_basic, Fr_grad with H = |.|_2);
 * ``energy``  -- F^a, F^r (eqs. global_minimization, attraction_term,
   repulsion_term);
+* ``attraction_at`` -- attraction force and potential of the density at
+  arbitrary points (the field of eq. attraction_derivative_basic);
 * ``project`` -- per-shot projection onto the constraint set (eq. constraints,
   Sec. II-D, Suppl. Sec. I) by FISTA on the dual;
 * ``violation`` -- the constraint checker;
@@ -58,6 +60,8 @@ def _load():
             lib.oracle_project.argtypes = [p, p, i64, i64, d, d, d, i64, p, i64, d, d, i64, p]
             lib.oracle_violation.argtypes = [p, i64, i64, d, d, d, i64, p, p]
             lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64]
+            lib.oracle_attraction_at.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p]
+            lib.oracle_attraction_at.restype = ctypes.c_int
             for f in (lib.oracle_forces, lib.oracle_energy, lib.oracle_project,
                       lib.oracle_violation, lib.oracle_step):
                 f.restype = ctypes.c_int
@@ -99,6 +103,20 @@ def forces(K, grid, targets=None, energies: bool = False):
     if st != OK:
         raise ValueError(f"oracle_forces failed ({st})")
     return (A, R, G, ea, er) if energies else (A, R, G)
+
+
+def attraction_at(points, grid):
+    """(A, phi): attraction force [M, 3] and potential [M] of the density at
+    arbitrary points (float64)."""
+    P = _f64(points).reshape(-1, 3)
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    A = np.empty_like(P)
+    phi = np.empty(P.shape[0])
+    st = _load().oracle_attraction_at(_ptr(P), P.shape[0], _ptr(rho), nx, ny, nz, lo, hi,
+                                      _ptr(A), _ptr(phi))
+    if st != OK:
+        raise ValueError(f"oracle_attraction_at failed ({st})")
+    return A, phi
 
 
 def energy(K, grid):

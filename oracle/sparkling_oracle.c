@@ -136,6 +136,25 @@ int oracle_forces(const double *K, int64_t N, const double *rho, int64_t nx, int
     return bad ? ORACLE_EINVAL : ORACLE_OK;
 }
 
+/* Attraction force A(y) = sum_q rho_q (y - x_q)/|y - x_q| and potential
+ * phi(y) = sum_q rho_q |y - x_q| at M arbitrary points P[M][3] (the field
+ * whose gradient enters eq. attraction_derivative_basic; the paper evaluates
+ * it on a grid and interpolates). Either output may be NULL. */
+int oracle_attraction_at(const double *P, int64_t M, const double *rho, int64_t nx, int64_t ny,
+                         int64_t nz, double lo, double hi, double *A, double *phi)
+{
+    if (!P || M < 0 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo))
+        return ORACLE_EINVAL;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < M; ++m) {
+        double a[3], e;
+        attraction_one(P[3 * m], P[3 * m + 1], P[3 * m + 2], rho, nx, ny, nz, lo, hi, a, &e);
+        if (A) { A[3 * m] = a[0]; A[3 * m + 1] = a[1]; A[3 * m + 2] = a[2]; }
+        if (phi) phi[m] = e;
+    }
+    return ORACLE_OK;
+}
+
 /* Energy F = F^a - F^r (eqs. global_minimization, attraction_term,
  * repulsion_term); the per-target sums are added in index order. */
 int oracle_energy(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,

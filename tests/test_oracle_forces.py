@@ -242,3 +242,20 @@ def test_invalid_arguments_rejected():
         oracle.forces(np.zeros((4, 3)), one_cell(), targets=[0, 9])
     with pytest.raises(ValueError):
         oracle.forces(np.zeros((4, 3)), inputs.Grid((2, 1, 1), 0.5, -0.5, np.ones((1, 1, 2), np.float32)))
+
+
+def test_attraction_at_points_matches_forces_and_closed_form():
+    """attraction_at evaluates the same attraction as forces (and its
+    per-target energy sum) at arbitrary points; at a point far from a
+    one-cell density it is the unit vector and the distance."""
+    p = inputs.make_problem("tiny")
+    idx = np.array([0, 3, 511, 1023])
+    A0, _, _, ea, _ = oracle.forces(p.K, p.grid, targets=idx, energies=True)
+    A, phi = oracle.attraction_at(p.K[idx], p.grid)
+    np.testing.assert_array_equal(A, A0)
+    np.testing.assert_array_equal(phi, ea)
+    pts = np.array([[0.3, -0.1, 0.2], [0.0, 0.0, 0.0]])
+    A1, phi1 = oracle.attraction_at(pts, one_cell(0.0, 0.2))   # cell centre (0.1, 0.1, 0.1)
+    d = pts - 0.1
+    np.testing.assert_allclose(A1, d / np.linalg.norm(d, axis=1, keepdims=True), atol=1e-15)
+    np.testing.assert_allclose(phi1, np.linalg.norm(d, axis=1), atol=1e-15)
