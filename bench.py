@@ -54,6 +54,10 @@ def parse_args(argv=None):
                     help="single-trajectory step through sparkling_step (separate pair kernels) "
                          "or the persistent engine (sparkling_step_batched with B = 1)")
     ap.add_argument("--acc", choices=("kahan", "fp64"), default="kahan")
+    ap.add_argument("--attraction", choices=("direct", "field"), default="direct",
+                    help="direct sum (exact) or the interpolated node field of the density "
+                         "(fast, approximate; the step's pairs are then counted as equivalent "
+                         "pair interactions)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -63,6 +67,8 @@ def parse_args(argv=None):
         a.steps = 1 if a.workload == "hr" else 3
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if a.attraction == "field" and (a.workload == "batched" or a.path == "engine"):
+        ap.error("--attraction field runs on the kernels path (the engine takes the direct sum)")
     return a
 
 
@@ -315,6 +321,13 @@ def run_ours(args):
     w.ctx = ctx
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    field_build_ms = None
+    if args.attraction == "field":
+        sp.sparkling_set_attraction(ctx, sp.ATTRACTION_FIELD)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sp.sparkling_attraction_field(ctx, w.grids[0])      # blocking
+        field_build_ms = (time.perf_counter() - t0) * 1e3
 
     for _ in range(args.warmup):
         w.step()
@@ -364,6 +377,10 @@ def run_ours(args):
     if w.batched:
         # one engine launch runs every pair of the step: N_b*P_b + N_b*(N_b-1)
         kname, kpairs = "engine", w.pairs
+    elif args.attraction == "field":
+        # the attraction is an interpolation; the symmetric repulsion takes
+        # one reciprocal square root per unordered pair
+        kname, kpairs = "repulsion", w.N * (w.N - 1) // 2
     else:
         p0 = w.probs[0]
         kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
@@ -438,12 +455,19 @@ def run_ours(args):
             "config": {"workload": w.desc, "N": w.N, "P": int(p0.grid.rho.size),
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
                        "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
-                       "l2": "flushed (512 MB write) between timed steps", "acc": args.acc},
+                       "l2": "flushed (512 MB write) between timed steps", "acc": args.acc,
+                       "attraction": args.attraction},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,
             "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
         }
+        if field_build_ms is not None:
+            out["field"] = {
+                "build_ms": field_build_ms,
+                "note": "node field of the density (FP64 FFT convolution, once per density, "
+                        "outside the timed steps); value counts N*P + N*(N-1) equivalent pairs; "
+                        "the e2e leg rebuilds the field every step (the density is copied in)"}
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:

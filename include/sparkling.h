@@ -120,6 +120,10 @@ typedef struct sparkling_proj {
 #define SPARKLING_KERNEL_ENGINE 5   /* a whole batched step (packs + persistent engine) */
 #define SPARKLING_KERNEL_COUNT 6
 
+/* How the attraction term is evaluated (sparkling_set_attraction). */
+#define SPARKLING_ATTRACTION_DIRECT 0   /* direct sum over the grid: O(N P) */
+#define SPARKLING_ATTRACTION_FIELD 1    /* interpolated node field: O(N), approximate */
+
 /* Flags of sparkling_step_batched. */
 #define SPARKLING_BATCH_GRAPH 1     /* replay the step from a cached CUDA graph */
 
@@ -285,6 +289,35 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
 /* Text of the tuning trials (pairs/s per shape) and of the choices, NUL
  * terminated, truncated to len bytes. */
 SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len);
+
+/* Attraction mode of the context's sparkling_grad, sparkling_energy,
+ * sparkling_energy_backward and sparkling_step calls (the batched step and
+ * sparkling_grad_noalloc always take the direct sum).
+ *   SPARKLING_ATTRACTION_DIRECT (default): the direct sum over the grid.
+ *   SPARKLING_ATTRACTION_FIELD: the fast summation of Sec. II-C.1 (eq.
+ *     attraction_derivative_basic).  The attraction force
+ *     E(y) = sum_q rho_q (y - x_q) / |y - x_q| and the attraction potential
+ *     phi(y) = sum_q rho_q |y - x_q| of the density are computed exactly (an
+ *     FP64 FFT convolution, stored as float) on the cell-centre nodes of the
+ *     grid extended by one node per side, (nx+2)(ny+2)(nz+2) nodes, and the
+ *     samples take their trilinear interpolation: O(N) work per evaluation
+ *     instead of O(N P).  It is an approximation; its error against the
+ *     direct sum is measured by the caller, not bounded here.  Samples
+ *     outside [lo, hi] take the value of the nearest boundary cell.
+ * Returns SPARKLING_E_INVAL for another mode. */
+SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
+
+/* Build the node field of `grid`'s density for SPARKLING_ATTRACTION_FIELD
+ * and keep it in the context (one field at a time, (n+2)^3 float4 on the
+ * device).  Calls in field mode build it themselves when the grid (rho
+ * pointer, n, lo, hi) differs from the one kept; call this again after
+ * changing the density values in place.  Allocates temporary FFT buffers of
+ * about 40 L^3 bytes, L = the smallest 2,3,5,7-smooth size >= 2n+1 per
+ * axis, and blocks until the field is ready.  Must not be called while
+ * `stream` is being captured.  Errors: SPARKLING_E_INVAL (bad grid),
+ * SPARKLING_E_NOMEM, SPARKLING_E_CUDA (CUDA or cuFFT failure). */
+SPARKLING_API int sparkling_attraction_field(sparkling_ctx *ctx, const sparkling_grid *grid,
+                                             void *stream);
 
 /* Number of kernels this context has launched since it was created. */
 SPARKLING_API int64_t sparkling_launch_count(const sparkling_ctx *ctx);

@@ -20,6 +20,7 @@ F32, F64 = 0, 1
 ACC_KAHAN32, ACC_FP64 = 0, 1
 KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine")
 BATCH_GRAPH = 1
+ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
 
 # Every entry point declared in include/sparkling.h.
 ABI_SYMBOLS = (
@@ -28,6 +29,7 @@ ABI_SYMBOLS = (
     "sparkling_step_host", "sparkling_status", "sparkling_set_timing", "sparkling_kernel_times",
     "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
+    "sparkling_set_attraction", "sparkling_attraction_field",
 )
 
 
@@ -84,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "sparkling_grad_noalloc": ([p, i, i64, ctypes.POINTER(Grid), i, p, i, p], i),
             "sparkling_set_autotune": ([p, i], i),
             "sparkling_tuning_report": ([p, p, i64], i),
+            "sparkling_set_attraction": ([p, i], i),
+            "sparkling_attraction_field": ([p, p, p], i),
             "sparkling_step_batched": ([p, ctypes.c_int32, p, p, i, ctypes.c_int32,
                                         ctypes.POINTER(Grid), p, ctypes.POINTER(Proj), i, i, p], i),
         }
@@ -330,6 +334,18 @@ def sparkling_tuning_report(ctx: Context) -> str:
     buf = ctypes.create_string_buffer(8192)
     _check(ctx, lib().sparkling_tuning_report(ctx.handle, buf, len(buf)))
     return buf.value.decode()
+
+
+def sparkling_set_attraction(ctx: Context, mode: int) -> None:
+    """ATTRACTION_DIRECT (direct sum, default) or ATTRACTION_FIELD
+    (interpolated node field of the density)."""
+    _check(ctx, lib().sparkling_set_attraction(ctx.handle, int(mode)))
+
+
+def sparkling_attraction_field(ctx: Context, grid: Grid, stream=None) -> None:
+    """(Re)build the node field of grid's density (blocking)."""
+    _check(ctx, lib().sparkling_attraction_field(ctx.handle, ctypes.byref(grid),
+                                                 _stream(stream)))
 
 
 def sparkling_launch_count(ctx: Context) -> int:

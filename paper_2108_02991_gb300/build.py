@@ -1,8 +1,9 @@
 """Build libsparkling.so (sm_103a) in-tree with nvcc.
 
-The three translation units are compiled in parallel and linked into one
-shared library with the CUDA runtime linked statically, exporting only the
-C ABI declared in include/sparkling.h.
+The translation units are compiled in parallel and linked into one shared
+library with the CUDA runtime linked statically and cuFFT dynamically (the
+node field of the fast attraction), exporting only the C ABI declared in
+include/sparkling.h.
 """
 from __future__ import annotations
 
@@ -17,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparkling.so")
-SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "repulsion_sym.cu", "project.cu", "noalloc.cu", "engine.cu"]
+SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "repulsion_sym.cu", "project.cu", "noalloc.cu",
+           "engine.cu", "field.cu"]
 HEADERS = ["kernels.h", "ptx.cuh", "pair_dev.cuh", "project_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -75,7 +77,9 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             print(line, file=sys.stderr)
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft", "-Xlinker",
+                                                              "-rpath," + cuda_lib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{r.stderr}")

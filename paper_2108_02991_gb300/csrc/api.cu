@@ -79,6 +79,14 @@ struct sparkling_ctx {
     size_t h_traj_cap = 0;
     int items_per_cta = 16;         // work-list granularity
     int engine_choice[2][2] = {{-1, -1}, {-1, -1}};   // [acc][K dtype] engine tile shape
+    // fast attraction: the node field of one density (field.cu)
+    int attr_mode = SPARKLING_ATTRACTION_DIRECT;
+    float4 *field = nullptr;
+    size_t field_cap = 0;
+    bool field_valid = false;
+    const void *field_rho = nullptr;
+    int field_n[3] = {0, 0, 0};
+    double field_lo = 0.0, field_hi = 0.0;
 };
 
 namespace {
@@ -266,7 +274,7 @@ struct PairPlan {
     int64_t tiles;
     int va, vr;            // tile shapes (autotuner variants) of the two pair kernels
     Split spa, spr;
-    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_racc, o_eblocks, o_g64, end;
+    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_racc, o_eblocks, o_g64, o_adir, end;
 };
 
 int ensure_occupancy(sparkling_ctx *ctx)
@@ -345,6 +353,7 @@ int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, 
     P.o_racc = cv.take((size_t)N * 3 * sizeof(unsigned long long));
     P.o_eblocks = cv.take((size_t)energy_blocks(N) * sizeof(double2));
     P.o_g64 = need_g64 ? cv.take((size_t)N * 3 * sizeof(double)) : 0;
+    P.o_adir = ctx->attr_mode == SPARKLING_ATTRACTION_FIELD ? cv.take((size_t)N * sizeof(dacc4)) : 0;
     P.end = cv.off;
     return SPARKLING_OK;
 }
@@ -446,8 +455,56 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
     return SPARKLING_OK;
 }
 
+bool field_matches(const sparkling_ctx *ctx, const sparkling_grid *g)
+{
+    return ctx->field_valid && ctx->field_rho == g->rho && ctx->field_n[0] == g->n[0] &&
+           ctx->field_n[1] == g->n[1] && ctx->field_n[2] == g->n[2] && ctx->field_lo == g->lo &&
+           ctx->field_hi == g->hi;
+}
+
+// (Re)build the node field of g's density into the context (blocking).
+int build_field(sparkling_ctx *ctx, const sparkling_grid *g, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(ctx, SPARKLING_E_INVAL,
+                    "the attraction field must be built outside stream capture "
+                    "(call sparkling_attraction_field first)");
+    const size_t bytes = field_bytes(g->n[0], g->n[1], g->n[2]);
+    ctx->field_valid = false;
+    if (bytes > ctx->field_cap) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->field);
+        ctx->field = nullptr;
+        ctx->field_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->field, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPARKLING_E_NOMEM, "field allocation of %zu bytes failed", bytes);
+        }
+        ctx->field_cap = bytes;
+    }
+    const char *what = "";
+    cudaError_t e = field_build(g->rho, g->n[0], g->n[1], g->n[2], g->lo, g->hi, ctx->field,
+                                ctx->sms, st, &what);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, SPARKLING_E_NOMEM, "attraction field: %s allocation failed", what);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    ctx->launches += 13;
+    ctx->field_valid = true;
+    ctx->field_rho = g->rho;
+    for (int a = 0; a < 3; ++a) ctx->field_n[a] = g->n[a];
+    ctx->field_lo = g->lo;
+    ctx->field_hi = g->hi;
+    return SPARKLING_OK;
+}
+
 // pack -> (autotune) -> attraction -> repulsion -> combine (gradient) or
-// energy reduction.
+// energy reduction.  In field mode the attraction is the interpolated node
+// field.
 int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_grid *g, int acc,
               bool energy, PairPlan &P, void *G, int G_dtype, void *A, void *R, bool g64,
               cudaStream_t st, double scale = 1.0, const double *scale_dev = nullptr)
@@ -455,6 +512,11 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     float4 *pos = at<float4>(ctx, P.o_pos);
     float *rho = at<float>(ctx, P.o_rho);
     float *coords = at<float>(ctx, P.o_coords);
+    const bool field_mode = ctx->attr_mode == SPARKLING_ATTRACTION_FIELD;
+    if (field_mode && !field_matches(ctx, g)) {
+        int s = build_field(ctx, g, st);
+        if (s) return s;
+    }
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_PACK, st);
         CK(launch_pack_positions(K, K_dtype, P.N, pos, ctx->d_status, ctx->sms, st));
@@ -472,7 +534,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     RepArgs ra;
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
-    const bool need_a = attr_choice_of(ctx, acc, P.gxp) < 0,
+    const bool need_a = !field_mode && attr_choice_of(ctx, acc, P.gxp) < 0,
                need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
                need_s = ctx->rep_symmetric && ctx->sym_choice < 0;
     if (ctx->autotune && (need_a || need_r || need_s)) {
@@ -488,9 +550,14 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     }
     aa.sp = P.spa;
     ra.sp = P.spr;
+    dacc4 *a_direct = field_mode ? at<dacc4>(ctx, P.o_adir) : nullptr;
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_ATTRACTION, st);
-        CK(launch_attraction(aa, acc, energy, P.va, st));
+        if (field_mode)
+            CK(launch_interp(pos, P.N, ctx->field, P.nx, P.ny, P.nz, g->lo, g->hi, a_direct,
+                             ctx->sms, st));
+        else
+            CK(launch_attraction(aa, acc, energy, P.va, st));
         ls.done();
     }
     unsigned long long *racc = nullptr;
@@ -516,6 +583,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     cb.G = G; cb.A = A; cb.R = R;
     cb.G64 = g64 ? at<double>(ctx, P.o_g64) : nullptr;
     cb.racc = racc;
+    cb.a_direct = a_direct;
     cb.scale = scale;
     cb.scale_dev = scale_dev;
     cb.energy_blocks = at<double2>(ctx, P.o_eblocks);
@@ -870,6 +938,7 @@ SPARKLING_API void sparkling_destroy(sparkling_ctx *ctx)
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         if (ctx->h_traj) cudaFreeHost(ctx->h_traj);
         cudaFree(ctx->ws);
+        cudaFree(ctx->field);
         cudaFree(ctx->h_K);
         cudaFree(ctx->h_rho);
         cudaFree(ctx->d_status);
@@ -1172,6 +1241,7 @@ SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dt
     CK(cudaMemcpyAsync(ctx->h_rho, rho_host, rb, cudaMemcpyHostToDevice, st));
     sparkling_grid g = *grid;
     g.rho = ctx->h_rho;
+    if (ctx->field_rho == ctx->h_rho) ctx->field_valid = false;   // new density values
     if ((s = sparkling_step(ctx, ctx->h_K, K_dtype, Nc, Ns, &g, acc, eta, proj, stream))) return s;
     CK(cudaMemcpyAsync(K_host, ctx->h_K, kb, cudaMemcpyDeviceToHost, st));
     return read_status(ctx, st);
@@ -1232,6 +1302,26 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable)
         ctx->autotune = true;
     }
     return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (mode != SPARKLING_ATTRACTION_DIRECT && mode != SPARKLING_ATTRACTION_FIELD)
+        return fail(ctx, SPARKLING_E_INVAL, "attraction mode %d is not DIRECT/FIELD", mode);
+    ctx->attr_mode = mode;
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_attraction_field(sparkling_ctx *ctx, const sparkling_grid *grid,
+                                             void *stream)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    int s;
+    if ((s = validate_grid(ctx, grid, true))) return s;
+    if ((s = lazy_init(ctx))) return s;
+    if (!is_device_ptr(grid->rho)) return fail(ctx, SPARKLING_E_INVAL, "grid->rho must be device memory");
+    return build_field(ctx, grid, static_cast<cudaStream_t>(stream));
 }
 
 SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len)

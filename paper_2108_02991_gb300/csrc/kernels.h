@@ -131,6 +131,7 @@ struct CombineArgs {
     void *G, *A, *R;      // outputs [N][3] (A, R may be null)
     double *G64;          // optional FP64 copy of G [N][3]
     const unsigned long long *racc;   // symmetric repulsion sums [N][NV] (replaces part_r)
+    const dacc4 *a_direct;            // attraction per target [N] (replaces part_a), or null
     double scale;         // G, A, R are multiplied by scale * (*scale_dev if set)
     const double *scale_dev;
     double2 *energy_blocks;  // energy mode: per-block (sum ea, sum er)
@@ -168,6 +169,13 @@ int repulsion_sym_ctas_per_sm(bool energy, int variant);
 cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st);
 int energy_blocks(int64_t N);
 cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream_t st);
+
+// Fast attraction (field.cu): node field of a density and its interpolation.
+size_t field_bytes(int nx, int ny, int nz);
+cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, double hi,
+                        float4 *field, int sms, cudaStream_t st, const char **what);
+cudaError_t launch_interp(const float4 *pos, int64_t N, const float4 *field, int nx, int ny, int nz,
+                          double lo, double hi, dacc4 *out, int sms, cudaStream_t st);
 
 // Projection (project.cu).
 struct ProjArgs {

@@ -209,7 +209,7 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     CombineArgs cb;
     cb.N = N; cb.part_a = part_a; cb.part_r = part_r; cb.spa = spa; cb.spr = spr;
     cb.G = G; cb.A = nullptr; cb.R = nullptr; cb.G64 = nullptr;
-    cb.scale = 1.0; cb.scale_dev = nullptr; cb.energy_blocks = nullptr; cb.racc = nullptr;
+    cb.scale = 1.0; cb.scale_dev = nullptr; cb.energy_blocks = nullptr; cb.racc = nullptr; cb.a_direct = nullptr;
     NA_CK(launch_combine(cb, G_dtype, sms, st));
     int h = 0;
     NA_CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -123,7 +123,7 @@ __global__ void combine_kernel(const CombineArgs c)
     const double sc = c.scale_dev ? c.scale * c.scale_dev[0] : c.scale;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        dacc4 a = sum_slots(c.part_a, c.spa, i);
+        dacc4 a = c.a_direct ? c.a_direct[i] : sum_slots(c.part_a, c.spa, i);
         dacc4 r;
         if (c.racc) {
             r.x = (double)(long long)c.racc[3 * i] / kFixScale;
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_block_kernel(const Comb
     for (int k = 0; k < kEnergyPerThread; ++k) {
         const int64_t i = (int64_t)blockIdx.x * kEnergyBlock + k * kEnergyThreads + threadIdx.x;
         if (i < c.N) {
-            ea += sum_slots(c.part_a, c.spa, i).w;
+            ea += c.a_direct ? c.a_direct[i].w : sum_slots(c.part_a, c.spa, i).w;
             er += c.racc ? (double)(long long)c.racc[i] / kFixScale : sum_slots(c.part_r, c.spr, i).w;
         }
     }

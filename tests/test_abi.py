@@ -133,6 +133,12 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert "margin" in msg
     assert L.sparkling_grad(None, dummy, 0, 10, ctypes.byref(g), 0, dummy, 0, None, None, None) == lib.E_INVAL
     assert "ctx" in lib.sparkling_last_error(None)
+    # attraction mode
+    assert L.sparkling_set_attraction(h, 7) == lib.E_INVAL
+    assert L.sparkling_set_attraction(h, lib.ATTRACTION_FIELD) == lib.OK
+    assert L.sparkling_attraction_field(h, None, None) == lib.E_INVAL
+    assert L.sparkling_attraction_field(h, ctypes.byref(bad), None) == lib.E_INVAL
+    assert L.sparkling_set_attraction(h, lib.ATTRACTION_DIRECT) == lib.OK
     assert lib.sparkling_launch_count(ctx) == 0
     lib.sparkling_destroy(ctx)
 

@@ -1,0 +1,183 @@
+"""Fast attraction (SPARKLING_ATTRACTION_FIELD, Sec. II-C.1): the attraction
+force and potential of the density are computed on the cell-centre nodes of
+the grid extended by one node per side and interpolated trilinearly at the
+samples.
+
+* at the nodes themselves the library must return the oracle's direct sums
+  (the FFT convolution is exact up to rounding; the field is stored as float);
+* elsewhere it must return the trilinear interpolation of those node values;
+* against the direct sum it is an approximation: its error on the synthetic
+  workloads is measured here and must stay below the bound stated in each
+  test (second order in the cell size).
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_02991_gb300 import build
+    build.build()
+    import paper_2108_02991_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sp):
+    c = sp.sparkling_create(0)
+    sp.sparkling_set_attraction(c, sp.ATTRACTION_FIELD)
+    yield c
+    c.close()
+
+
+def random_grid(nx, ny, nz, seed, lo=-0.5, hi=0.5):
+    rho = np.random.default_rng(seed).uniform(0.0, 1.0, size=(nz, ny, nx))
+    rho = (rho / rho.sum()).astype(np.float32)
+    return inputs.Grid((nx, ny, nz), lo, hi, rho)
+
+
+def node_axes(grid):
+    """Node coordinates per axis: lo + (m + 1/2) h, m = -1 .. n."""
+    h = [(grid.hi - grid.lo) / n for n in grid.n]
+    return [grid.lo + (np.arange(-1, n + 1) + 0.5) * h[a] for a, n in enumerate(grid.n)]
+
+
+def node_field(grid):
+    """Oracle values (A, phi) at every node, shape [nz+2][ny+2][nx+2][4]."""
+    x, y, z = node_axes(grid)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    A, phi = oracle.attraction_at(P, grid)
+    nx, ny, nz = grid.n
+    return np.concatenate([A, phi[:, None]], 1).reshape(nz + 2, ny + 2, nx + 2, 4), P
+
+
+def trilinear(F, grid, P):
+    """Trilinear interpolation of node values F at points P (clamped to the
+    outermost cell outside the box)."""
+    out = np.zeros((P.shape[0], F.shape[-1]))
+    o, f = [], []
+    for a, n in enumerate(grid.n):
+        h = (grid.hi - grid.lo) / n
+        u = (P[:, a] - grid.lo) / h + 0.5
+        oa = np.clip(np.floor(u).astype(np.int64), 0, n)
+        o.append(oa)
+        f.append(np.clip(u - oa, 0.0, 1.0))
+    for c in range(8):
+        d = (c & 1, (c >> 1) & 1, c >> 2)
+        w = np.ones(P.shape[0])
+        for a in range(3):
+            w = w * (f[a] if d[a] else 1.0 - f[a])
+        out += w[:, None] * F[o[2] + d[2], o[1] + d[1], o[0] + d[0]]
+    return out
+
+
+def field_grad(sp, ctx, K, grid, energy=False):
+    Kd = torch.from_numpy(np.ascontiguousarray(K, np.float32)).cuda()
+    rho = torch.from_numpy(grid.rho).cuda()
+    g = sp.make_grid(rho, grid.lo, grid.hi, grid.n)
+    G = torch.empty(K.shape[0], 3, dtype=torch.float64, device="cuda")
+    A = torch.empty_like(G)
+    sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G, A=A)
+    sp.sparkling_status(ctx)
+    out = [A.cpu().numpy(), G.cpu().numpy()]
+    if energy:
+        out.append(sp.sparkling_energy(ctx, Kd, g, sp.ACC_KAHAN32))
+    return out
+
+
+def test_field_at_nodes_equals_direct_sum(sp, ctx):
+    """Samples placed exactly on every node (dyadic cell sizes, so that the
+    float32 positions are exact): A equals the oracle's direct sum to the
+    rounding of the float field, and the attraction energy is the mean of
+    the oracle's potential."""
+    grid = random_grid(16, 32, 8, seed=11)
+    F, P = node_field(grid)
+    A, _, (Fval, Fa, _) = field_grad(sp, ctx, P, grid, energy=True)
+    ref = F.reshape(-1, 4)
+    err = np.abs(A - ref[:, :3])
+    tol = 2.0 ** -23 * np.abs(ref[:, :3]) + 1e-13
+    assert np.all(err <= tol), f"node field off by {err.max():.3e}"
+    want = ref[:, 3].mean()
+    assert abs(Fa - want) <= 1e-6 * want, (Fa, want)
+
+
+def test_field_interpolation_of_node_values(sp, ctx):
+    """Random samples in and just outside the box (non-dyadic, uneven grid):
+    the result is the trilinear interpolation of the oracle's node values."""
+    grid = random_grid(20, 12, 9, seed=12, lo=-0.5, hi=0.5)
+    F, _ = node_field(grid)
+    rng = np.random.default_rng(13)
+    P = rng.uniform(-0.56, 0.56, size=(5000, 3)).astype(np.float32)
+    A, _, (_, Fa, _) = field_grad(sp, ctx, P, grid, energy=True)
+    want = trilinear(F, grid, P.astype(np.float64))
+    scale = np.abs(F[..., :3]).max()
+    assert np.abs(A - want[:, :3]).max() <= 1e-6 * scale
+    assert abs(Fa - want[:, 3].mean()) <= 1e-6 * want[:, 3].mean()
+
+
+def test_field_error_against_direct_sum_small(sp, ctx):
+    """The 64 x 1024 spokes on the 64^3 inverse-square density: the field
+    attraction against the direct sum of the oracle on 512 sampled targets.
+    Trilinear interpolation of a field whose terms bend on the scale of the
+    cell gives a second-order error; at 64^3 the relative L2 error of A is
+    below 1e-3 (measured about 2e-4 on uniform samples)."""
+    p = inputs.make_problem("small")
+    idx = np.sort(np.random.default_rng(14).choice(p.N, size=512, replace=False))
+    A, G = field_grad(sp, ctx, p.K, p.grid)
+    A0, _, G0 = oracle.forces(p.K.astype(np.float64), p.grid, targets=idx)
+    eA = rel_l2(A[idx], A0)
+    eG = rel_l2(G[idx], G0)
+    print(f"field attraction 64^3: A rel L2 {eA:.3e}, G rel L2 {eG:.3e}")
+    assert eA < 1e-3
+    assert eG < 1e-2
+
+
+def test_field_rebuilt_after_density_change(sp, ctx):
+    """The context keeps one field; a new density (another grid) rebuilds
+    it, and sparkling_attraction_field refreshes it after an in-place change."""
+    g1 = random_grid(8, 8, 8, seed=21)
+    g2 = random_grid(8, 8, 8, seed=22)
+    x, y, z = node_axes(g1)
+    P = np.array([[x[3], y[4], z[5]], [x[1], y[8], z[2]]], dtype=np.float32)
+    rho = torch.from_numpy(g1.rho).cuda()
+    g = sp.make_grid(rho, g1.lo, g1.hi, g1.n)
+    Kd = torch.from_numpy(P).cuda()
+    G = torch.empty(2, 3, dtype=torch.float64, device="cuda")
+    A = torch.empty_like(G)
+    sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G, A=A)
+    sp.sparkling_status(ctx)
+    A1, _ = oracle.attraction_at(P.astype(np.float64), g1)
+    np.testing.assert_allclose(A.cpu().numpy(), A1, rtol=0, atol=2e-7)
+    rho.copy_(torch.from_numpy(g2.rho))          # same pointer, new values
+    sp.sparkling_attraction_field(ctx, g)
+    sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G, A=A)
+    sp.sparkling_status(ctx)
+    A2, _ = oracle.attraction_at(P.astype(np.float64), g2)
+    np.testing.assert_allclose(A.cpu().numpy(), A2, rtol=0, atol=2e-7)
+
+
+
+def test_field_error_against_direct_sum_diff(sp, ctx):
+    """N = 1,048,576 spokes on the 192^3 density rho ~ 1/|x|^1.5: the field
+    attraction against the oracle's direct sum on 256 sampled targets.  With
+    a second-order error, the 64^3 bound scaled by (64/192)^2 applies."""
+    p = inputs.make_problem("diff")
+    idx = np.sort(np.random.default_rng(15).choice(p.N, size=256, replace=False))
+    A, G = field_grad(sp, ctx, p.K, p.grid)
+    A0, _, G0 = oracle.forces(p.K.astype(np.float64), p.grid, targets=idx)
+    eA = rel_l2(A[idx], A0)
+    eG = rel_l2(G[idx], G0)
+    print(f"field attraction 192^3: A rel L2 {eA:.3e}, G rel L2 {eG:.3e}")
+    assert eA < 1e-3 / 9
+    assert eG < 1e-2 / 9
