@@ -311,7 +311,8 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
  * and keep it in the context (one field at a time, (n+2)^3 float4 on the
  * device).  Calls in field mode build it themselves when the grid (rho
  * pointer, n, lo, hi) differs from the one kept; call this again after
- * changing the density values in place.  Allocates temporary FFT buffers of
+ * changing the density values in place (or after placing another density
+ * of the same shape at the same address).  Allocates temporary FFT buffers of
  * about 40 L^3 bytes, L = the smallest 2,3,5,7-smooth size >= 2n+1 per
  * axis, and blocks until the field is ready.  Must not be called while
  * `stream` is being captured.  Errors: SPARKLING_E_INVAL (bad grid),
