@@ -290,6 +290,19 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
  * terminated, truncated to len bytes. */
 SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len);
 
+/* Kernel of the energy: H(r) = sqrt(r^2 + eps^2), the regularised norm of
+ * Sec. II-C (choice of step size), whose gradient is Lipschitz (constant
+ * 1/eps), so that a fixed step proportional to eps converges.  eps = 0 (the
+ * default) is the plain norm H(r) = r of the rest of the paper.  Applies to
+ * every later sparkling_grad, sparkling_energy, sparkling_energy_backward,
+ * sparkling_step, sparkling_step_host and sparkling_step_batched call of the
+ * context and to the attraction field (not to sparkling_grad_noalloc, which
+ * has no context and always takes eps = 0).  The pair kernels add eps^2,
+ * rounded to float, to every squared distance; the energy leaves out the N
+ * self pairs (i = j), as F^r does.  Returns SPARKLING_E_INVAL unless
+ * 0 <= eps <= 1e3. */
+SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps);
+
 /* Attraction mode of the context's sparkling_grad, sparkling_energy,
  * sparkling_energy_backward and sparkling_step calls (the batched step and
  * sparkling_grad_noalloc always take the direct sum).

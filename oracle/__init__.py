@@ -18,6 +18,9 @@ NumPy arrays.  See the C file for the definitions followed:
   Sec. II-D, Suppl. Sec. I) by FISTA on the dual;
 * ``violation`` -- the constraint checker;
 * ``step``    -- one projected-gradient step (eq. proj_grad_descent).
+
+``forces``, ``energy``, ``attraction_at`` and ``step`` take ``eps`` for the
+regularised kernel H(r) = sqrt(r^2 + eps^2) (Sec. II-C, choice of step size).
 """
 from __future__ import annotations
 
@@ -55,12 +58,12 @@ def _load():
             build()
             lib = ctypes.CDLL(_LIB)
             d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
-            lib.oracle_forces.argtypes = [p, i64, p, i64, i64, i64, d, d, p, i64, p, p, p, p, p]
-            lib.oracle_energy.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p]
+            lib.oracle_forces.argtypes = [p, i64, p, i64, i64, i64, d, d, p, i64, p, p, p, p, p, d]
+            lib.oracle_energy.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p, d]
             lib.oracle_project.argtypes = [p, p, i64, i64, d, d, d, i64, p, i64, d, d, i64, p]
             lib.oracle_violation.argtypes = [p, i64, i64, d, d, d, i64, p, p]
-            lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64]
-            lib.oracle_attraction_at.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p]
+            lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64, d]
+            lib.oracle_attraction_at.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p, d]
             lib.oracle_attraction_at.restype = ctypes.c_int
             for f in (lib.oracle_forces, lib.oracle_energy, lib.oracle_project,
                       lib.oracle_violation, lib.oracle_step):
@@ -85,9 +88,10 @@ def _grid_args(grid):
     return rho, nx, ny, nz, float(grid.lo), float(grid.hi)
 
 
-def forces(K, grid, targets=None, energies: bool = False):
+def forces(K, grid, targets=None, energies: bool = False, eps: float = 0.0):
     """Return (A, R, G) as float64 [M, 3] for the target indices (all if None);
-    with ``energies`` also the per-target sums (ea, er)."""
+    with ``energies`` also the per-target sums (ea, er).  eps > 0: kernel
+    sqrt(r^2 + eps^2)."""
     K = _f64(K)
     N = K.shape[0]
     rho, nx, ny, nz, lo, hi = _grid_args(grid)
@@ -99,13 +103,13 @@ def forces(K, grid, targets=None, energies: bool = False):
     A = np.empty((M, 3)); R = np.empty((M, 3)); G = np.empty((M, 3))
     ea = np.empty(M); er = np.empty(M)
     st = _load().oracle_forces(_ptr(K), N, _ptr(rho), nx, ny, nz, lo, hi, tptr, M,
-                               _ptr(A), _ptr(R), _ptr(G), _ptr(ea), _ptr(er))
+                               _ptr(A), _ptr(R), _ptr(G), _ptr(ea), _ptr(er), float(eps))
     if st != OK:
         raise ValueError(f"oracle_forces failed ({st})")
     return (A, R, G, ea, er) if energies else (A, R, G)
 
 
-def attraction_at(points, grid):
+def attraction_at(points, grid, eps: float = 0.0):
     """(A, phi): attraction force [M, 3] and potential [M] of the density at
     arbitrary points (float64)."""
     P = _f64(points).reshape(-1, 3)
@@ -113,19 +117,19 @@ def attraction_at(points, grid):
     A = np.empty_like(P)
     phi = np.empty(P.shape[0])
     st = _load().oracle_attraction_at(_ptr(P), P.shape[0], _ptr(rho), nx, ny, nz, lo, hi,
-                                      _ptr(A), _ptr(phi))
+                                      _ptr(A), _ptr(phi), float(eps))
     if st != OK:
         raise ValueError(f"oracle_attraction_at failed ({st})")
     return A, phi
 
 
-def energy(K, grid):
+def energy(K, grid, eps: float = 0.0):
     """Return (F, F^a, F^r)."""
     K = _f64(K)
     rho, nx, ny, nz, lo, hi = _grid_args(grid)
     fa, fr = ctypes.c_double(), ctypes.c_double()
     st = _load().oracle_energy(_ptr(K), K.shape[0], _ptr(rho), nx, ny, nz, lo, hi,
-                               ctypes.byref(fa), ctypes.byref(fr))
+                               ctypes.byref(fa), ctypes.byref(fr), float(eps))
     if st != OK:
         raise ValueError(f"oracle_energy failed ({st})")
     return fa.value - fr.value, fa.value, fr.value
@@ -164,13 +168,13 @@ def violation(K, Nc, Ns, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0)
 
 
 def step(K, Nc, Ns, grid, eta, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0),
-         n_iter=100):
+         n_iter=100, eps: float = 0.0):
     """One projected-gradient step K <- Pi(K - eta G); returns a new array."""
     K = _f64(K).reshape(-1, 3).copy()
     rho, nx, ny, nz, lo, hi = _grid_args(grid)
     pin_a = _f64(pin)
     st = _load().oracle_step(_ptr(K), Nc, Ns, _ptr(rho), nx, ny, nz, lo, hi, eta, alpha, beta,
-                             box, pin_index, _ptr(pin_a), n_iter)
+                             box, pin_index, _ptr(pin_a), n_iter, float(eps))
     if st != OK:
         raise ValueError(f"oracle_step failed ({st})")
     return K

@@ -22,6 +22,13 @@
  * A term whose difference vector is exactly zero contributes nothing (the
  * minimum-norm subgradient of |.| at 0; the paper only excludes j = i).
  *
+ * Every entry point also takes eps >= 0 for the regularised kernel
+ * H(r) = sqrt(r^2 + eps^2) of Sec. II-C (choice of step size): each |d|
+ * above becomes |d|_eps = sqrt(|d|^2 + eps^2) and each unit vector
+ * d / |d| becomes d / |d|_eps (the gradient of |d|_eps).  eps = 0 is the
+ * plain norm; with eps > 0 no term is singular and none is skipped (F^r
+ * still sums over j != i only).
+ *
  * Projection (Sec. II-D and Suppl. Sec. I): each shot s in R^{Ns x 3} is
  * projected onto {|s|_inf <= box, s[pin] = v, |D1 s|_{2,inf} <= alpha,
  * |D2 s|_{2,inf} <= beta} (eq. constraints) by accelerated proximal gradient
@@ -53,7 +60,7 @@ static double centre(int64_t q, int64_t n, double lo, double hi)
 /* Attraction force and energy sum of one target position (kx,ky,kz). */
 static void attraction_one(double kx, double ky, double kz, const double *rho,
                            int64_t nx, int64_t ny, int64_t nz, double lo, double hi,
-                           double out[3], double *energy)
+                           double eps, double out[3], double *energy)
 {
     double ax = 0.0, ay = 0.0, az = 0.0, e = 0.0;
     for (int64_t iz = 0; iz < nz; ++iz) {
@@ -64,7 +71,7 @@ static void attraction_one(double kx, double ky, double kz, const double *rho,
             for (int64_t ix = 0; ix < nx; ++ix) {
                 double x = centre(ix, nx, lo, hi);
                 double dx = kx - x, dy = ky - y, dz = kz - z;
-                double r = sqrt(dx * dx + dy * dy + dz * dz);
+                double r = sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
                 if (r == 0.0)
                     continue;
                 double w = row[ix];
@@ -81,7 +88,8 @@ static void attraction_one(double kx, double ky, double kz, const double *rho,
 
 /* Sum over j != i of the unit vectors (K_i - K_j)/|K_i - K_j| and of the
  * distances |K_i - K_j| (not yet scaled by 1/N). */
-static void repulsion_one(const double *K, int64_t N, int64_t i, double out[3], double *energy)
+static void repulsion_one(const double *K, int64_t N, int64_t i, double eps, double out[3],
+                          double *energy)
 {
     double kx = K[3 * i], ky = K[3 * i + 1], kz = K[3 * i + 2];
     double rx = 0.0, ry = 0.0, rz = 0.0, e = 0.0;
@@ -89,7 +97,7 @@ static void repulsion_one(const double *K, int64_t N, int64_t i, double out[3], 
         if (j == i)
             continue;
         double dx = kx - K[3 * j], dy = ky - K[3 * j + 1], dz = kz - K[3 * j + 2];
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double r = sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
         if (r == 0.0)
             continue;
         rx += dx / r;
@@ -109,9 +117,9 @@ static void repulsion_one(const double *K, int64_t N, int64_t i, double out[3], 
  */
 int oracle_forces(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,
                   int64_t nz, double lo, double hi, const int64_t *targets, int64_t M,
-                  double *A, double *R, double *G, double *ea, double *er)
+                  double *A, double *R, double *G, double *ea, double *er, double eps)
 {
-    if (!K || N < 1 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo) || M < 0)
+    if (!K || N < 1 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo) || M < 0 || !(eps >= 0.0))
         return ORACLE_EINVAL;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
@@ -122,8 +130,8 @@ int oracle_forces(const double *K, int64_t N, const double *rho, int64_t nx, int
             continue;
         }
         double a[3], r[3], eA, eR;
-        attraction_one(K[3 * i], K[3 * i + 1], K[3 * i + 2], rho, nx, ny, nz, lo, hi, a, &eA);
-        repulsion_one(K, N, i, r, &eR);
+        attraction_one(K[3 * i], K[3 * i + 1], K[3 * i + 2], rho, nx, ny, nz, lo, hi, eps, a, &eA);
+        repulsion_one(K, N, i, eps, r, &eR);
         for (int c = 0; c < 3; ++c) {
             double rc = r[c] / (double)N;
             if (A) A[3 * m + c] = a[c];
@@ -141,14 +149,14 @@ int oracle_forces(const double *K, int64_t N, const double *rho, int64_t nx, int
  * whose gradient enters eq. attraction_derivative_basic; the paper evaluates
  * it on a grid and interpolates). Either output may be NULL. */
 int oracle_attraction_at(const double *P, int64_t M, const double *rho, int64_t nx, int64_t ny,
-                         int64_t nz, double lo, double hi, double *A, double *phi)
+                         int64_t nz, double lo, double hi, double *A, double *phi, double eps)
 {
-    if (!P || M < 0 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo))
+    if (!P || M < 0 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo) || !(eps >= 0.0))
         return ORACLE_EINVAL;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
         double a[3], e;
-        attraction_one(P[3 * m], P[3 * m + 1], P[3 * m + 2], rho, nx, ny, nz, lo, hi, a, &e);
+        attraction_one(P[3 * m], P[3 * m + 1], P[3 * m + 2], rho, nx, ny, nz, lo, hi, eps, a, &e);
         if (A) { A[3 * m] = a[0]; A[3 * m + 1] = a[1]; A[3 * m + 2] = a[2]; }
         if (phi) phi[m] = e;
     }
@@ -158,7 +166,7 @@ int oracle_attraction_at(const double *P, int64_t M, const double *rho, int64_t 
 /* Energy F = F^a - F^r (eqs. global_minimization, attraction_term,
  * repulsion_term); the per-target sums are added in index order. */
 int oracle_energy(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,
-                  int64_t nz, double lo, double hi, double *Fa, double *Fr)
+                  int64_t nz, double lo, double hi, double *Fa, double *Fr, double eps)
 {
     double *ea = (double *)malloc(sizeof(double) * (size_t)N);
     double *er = (double *)malloc(sizeof(double) * (size_t)N);
@@ -166,7 +174,7 @@ int oracle_energy(const double *K, int64_t N, const double *rho, int64_t nx, int
         free(ea); free(er);
         return ORACLE_EINVAL;
     }
-    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, NULL, ea, er);
+    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, NULL, ea, er, eps);
     if (st == ORACLE_OK) {
         double sa = 0.0, sr = 0.0;
         for (int64_t i = 0; i < N; ++i) {
@@ -401,12 +409,12 @@ int oracle_violation(const double *K, int64_t Nc, int64_t Ns, double alpha, doub
  * G = N dF/dK): K <- Pi(K - eta G), in place, K is [Nc*Ns][3]. */
 int oracle_step(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_t nx, int64_t ny,
                 int64_t nz, double lo, double hi, double eta, double alpha, double beta, double box,
-                int64_t pin_index, const double *pin, int64_t n_iter)
+                int64_t pin_index, const double *pin, int64_t n_iter, double eps)
 {
     int64_t N = Nc * Ns;
     double *G = (double *)malloc(sizeof(double) * (size_t)(3 * N));
     if (!G) return ORACLE_EINVAL;
-    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, G, NULL, NULL);
+    int st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, G, NULL, NULL, eps);
     if (st == ORACLE_OK) {
         for (int64_t m = 0; m < 3 * N; ++m)
             G[m] = K[m] - eta * G[m];

@@ -29,7 +29,7 @@ ABI_SYMBOLS = (
     "sparkling_step_host", "sparkling_status", "sparkling_set_timing", "sparkling_kernel_times",
     "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
-    "sparkling_set_attraction", "sparkling_attraction_field",
+    "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
 )
 
 
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "sparkling_tuning_report": ([p, p, i64], i),
             "sparkling_set_attraction": ([p, i], i),
             "sparkling_attraction_field": ([p, p, p], i),
+            "sparkling_set_regularisation": ([p, ctypes.c_double], i),
             "sparkling_step_batched": ([p, ctypes.c_int32, p, p, i, ctypes.c_int32,
                                         ctypes.POINTER(Grid), p, ctypes.POINTER(Proj), i, i, p], i),
         }
@@ -340,6 +341,11 @@ def sparkling_set_attraction(ctx: Context, mode: int) -> None:
     """ATTRACTION_DIRECT (direct sum, default) or ATTRACTION_FIELD
     (interpolated node field of the density)."""
     _check(ctx, lib().sparkling_set_attraction(ctx.handle, int(mode)))
+
+
+def sparkling_set_regularisation(ctx: Context, eps: float) -> None:
+    """Kernel H(r) = sqrt(r^2 + eps^2) for the context's later calls (0: |r|)."""
+    _check(ctx, lib().sparkling_set_regularisation(ctx.handle, float(eps)))
 
 
 def sparkling_attraction_field(ctx: Context, grid: Grid, stream=None) -> None:

@@ -72,6 +72,7 @@ struct sparkling_ctx {
         cudaGraphExec_t exec = nullptr;
         std::vector<const void *> graph_key;
         int graph_variant = -1;
+        float graph_eps2 = -1.f;          // eps^2 baked into the captured launch
         int eager_calls = 0;
     } batch;
     cudaStream_t cap_stream = nullptr;  // private stream the batched step is captured on
@@ -86,12 +87,21 @@ struct sparkling_ctx {
     bool field_valid = false;
     const void *field_rho = nullptr;
     int field_n[3] = {0, 0, 0};
-    double field_lo = 0.0, field_hi = 0.0;
+    double field_lo = 0.0, field_hi = 0.0, field_eps = 0.0;
+    // kernel H(r) = sqrt(r^2 + eps^2); eps = 0 is the plain norm
+    double eps = 0.0;
 };
 
 namespace {
 
 thread_local std::string g_err = "no error";
+
+// eps^2 as the pair kernels add it to r^2 (never below the zero-distance guard)
+float eps2_of(const sparkling_ctx *ctx)
+{
+    const float e2 = (float)(ctx->eps * ctx->eps);
+    return e2 > kEps2 ? e2 : kEps2;
+}
 
 int fail(sparkling_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -433,7 +443,7 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
         tt = std::max<int64_t>(1, std::min<int64_t>(tt, P.tiles));
         SymArgs sa;
         sa.pos = ra.pos; sa.N = std::min<int64_t>(P.N, tt * kTile); sa.tiles = tt;
-        sa.acc = racc; sa.status = ctx->d_status;
+        sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2; sa.eps2 = ra.eps2;
         int best = 0;
         double best_rate = 0.0;
         for (int v = 0; v < kSymVariants; ++v) {
@@ -459,7 +469,7 @@ bool field_matches(const sparkling_ctx *ctx, const sparkling_grid *g)
 {
     return ctx->field_valid && ctx->field_rho == g->rho && ctx->field_n[0] == g->n[0] &&
            ctx->field_n[1] == g->n[1] && ctx->field_n[2] == g->n[2] && ctx->field_lo == g->lo &&
-           ctx->field_hi == g->hi;
+           ctx->field_hi == g->hi && ctx->field_eps == ctx->eps;
 }
 
 // (Re)build the node field of g's density into the context (blocking).
@@ -486,8 +496,8 @@ int build_field(sparkling_ctx *ctx, const sparkling_grid *g, cudaStream_t st)
         ctx->field_cap = bytes;
     }
     const char *what = "";
-    cudaError_t e = field_build(g->rho, g->n[0], g->n[1], g->n[2], g->lo, g->hi, ctx->field,
-                                ctx->sms, st, &what);
+    cudaError_t e = field_build(g->rho, g->n[0], g->n[1], g->n[2], g->lo, g->hi, ctx->eps,
+                                ctx->field, ctx->sms, st, &what);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return fail(ctx, SPARKLING_E_NOMEM, "attraction field: %s allocation failed", what);
@@ -499,6 +509,7 @@ int build_field(sparkling_ctx *ctx, const sparkling_grid *g, cudaStream_t st)
     for (int a = 0; a < 3; ++a) ctx->field_n[a] = g->n[a];
     ctx->field_lo = g->lo;
     ctx->field_hi = g->hi;
+    ctx->field_eps = ctx->eps;
     return SPARKLING_OK;
 }
 
@@ -531,9 +542,11 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     aa.hx = (float)((g->hi - g->lo) / P.nx);
     aa.x0 = g->lo + 0.5 * ((g->hi - g->lo) / P.nx);
     aa.part = at<dacc4>(ctx, P.o_parta); aa.status = ctx->d_status;
+    aa.eps2 = eps2_of(ctx);
     RepArgs ra;
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
+    ra.eps2 = aa.eps2;
     const bool need_a = !field_mode && attr_choice_of(ctx, acc, P.gxp) < 0,
                need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
                need_s = ctx->rep_symmetric && ctx->sym_choice < 0;
@@ -586,6 +599,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     cb.a_direct = a_direct;
     cb.scale = scale;
     cb.scale_dev = scale_dev;
+    cb.eps = ctx->eps;
     cb.energy_blocks = at<double2>(ctx, P.o_eblocks);
     {
         LaunchScope ls(ctx, SPARKLING_KERNEL_COMBINE, st);
@@ -856,6 +870,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.done = e.queue + 1;
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
     e.status = ctx->d_status;
+    e.eps2 = eps2_of(ctx);
     const int ctas = ctx->sms * engine_ctas_per_sm(acc, K_dtype, variant);
     CK(launch_engine(e, acc, K_dtype, variant, std::min(ctas, b.ctas), st));
     return SPARKLING_OK;
@@ -1172,7 +1187,8 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     for (int t = 0; t < B; ++t) key.push_back(grids[t].rho);
     const bool use_graph = (flags & SPARKLING_BATCH_GRAPH) && cap == cudaStreamCaptureStatusNone;
     LaunchScope ls(ctx, SPARKLING_KERNEL_ENGINE, st);
-    if (use_graph && b.exec && b.graph_key == key && b.graph_variant == variant) {
+    if (use_graph && b.exec && b.graph_key == key && b.graph_variant == variant &&
+        b.graph_eps2 == eps2_of(ctx)) {
         CK(cudaGraphLaunch(b.exec, st));
     } else if (use_graph && b.eager_calls > 0) {
         // Capture (which records without executing) on a private stream --
@@ -1192,6 +1208,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         if (e != cudaSuccess) { b.exec = nullptr; return cuda_fail(ctx, e, "cudaGraphInstantiate"); }
         b.graph_key = key;
         b.graph_variant = variant;
+        b.graph_eps2 = eps2_of(ctx);
         CK(cudaGraphLaunch(b.exec, st));
     } else {
         if ((s = batch_device_work(ctx, K, K_dtype, grids, acc, variant, st))) return s;
@@ -1310,6 +1327,15 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode)
     if (mode != SPARKLING_ATTRACTION_DIRECT && mode != SPARKLING_ATTRACTION_FIELD)
         return fail(ctx, SPARKLING_E_INVAL, "attraction mode %d is not DIRECT/FIELD", mode);
     ctx->attr_mode = mode;
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (!(eps >= 0.0) || !std::isfinite(eps) || eps > 1e3)
+        return fail(ctx, SPARKLING_E_INVAL, "eps = %g must be finite, in [0, 1e3]", eps);
+    ctx->eps = eps;
     return SPARKLING_OK;
 }
 

@@ -92,6 +92,7 @@ __device__ __forceinline__ AttrArgs attr_args(const EngineTraj &t, const EngineA
     a.sp.units = 0; a.sp.per_tile = 0; a.sp.ctas = 1;
     a.sp.slots = t.slots;
     a.part = e.part + t.part_off;
+    a.eps2 = e.eps2;
     a.status = e.status;
     return a;
 }
@@ -104,6 +105,7 @@ __device__ __forceinline__ RepArgs rep_args(const EngineTraj &t, const EngineArg
     r.sp.units = 0; r.sp.per_tile = 0; r.sp.ctas = 1;
     r.sp.slots = t.slots;
     r.part = e.part + t.part_off;
+    r.eps2 = e.eps2;
     r.status = e.status;
     return r;
 }

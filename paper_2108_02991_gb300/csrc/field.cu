@@ -23,10 +23,11 @@ namespace sparkling {
 namespace {
 
 // Kernel samples on the periodic box: component c of k(d) at the offset
-// d = (dx, dy, dz) (in cells) whose residue is the array index.  c 0..2:
-// (d h)_c / |d h| (0 at d = 0); c 3: |d h|.
+// d = (dx, dy, dz) (in cells) whose residue is the array index.  With
+// |p|_eps = sqrt(|p|^2 + eps^2) and p = d h: c 0..2: p_c / |p|_eps (0 at
+// d = 0); c 3: |p|_eps.
 __global__ void fill_kernel_kernel(double *out, int Lx, int Ly, int Lz, double hx, double hy,
-                                   double hz, int c)
+                                   double hz, double eps2, int c)
 {
     const int64_t total = (int64_t)Lx * Ly * Lz;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -37,7 +38,7 @@ __global__ void fill_kernel_kernel(double *out, int Lx, int Ly, int Lz, double h
         const int dy = iy <= Ly / 2 ? iy : iy - Ly;
         const int dz = iz <= Lz / 2 ? iz : iz - Lz;
         const double px = dx * hx, py = dy * hy, pz = dz * hz;
-        const double r = sqrt(px * px + py * py + pz * pz);
+        const double r = sqrt(px * px + py * py + pz * pz + eps2);
         double v;
         if (c == 3) v = r;
         else v = r > 0.0 ? (c == 0 ? px : (c == 1 ? py : pz)) / r : 0.0;
@@ -158,7 +159,7 @@ size_t field_bytes(int nx, int ny, int nz)
 
 // Build the (E, phi) node field of a density into `field` (field_bytes).
 // Allocates its FFT buffers and plans for the duration of the call.
-cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, double hi,
+cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, double hi, double eps,
                         float4 *field, int sms, cudaStream_t st, const char **what)
 {
     const int Lx = nice_size(2 * nx + 1), Ly = nice_size(2 * ny + 1), Lz = nice_size(2 * nz + 1);
@@ -195,7 +196,7 @@ cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, dou
     if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
     if (cufftExecD2Z(fwd, real, rhat) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
     for (int c = 0; c < 4; ++c) {
-        fill_kernel_kernel<<<gr, 256, 0, st>>>(real, Lx, Ly, Lz, hx, hy, hz, c);
+        fill_kernel_kernel<<<gr, 256, 0, st>>>(real, Lx, Ly, Lz, hx, hy, hz, eps * eps, c);
         if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
         if (cufftExecD2Z(fwd, real, khat) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
         spectral_product_kernel<<<gc, 256, 0, st>>>(khat, rhat, ncplx, 1.0 / (double)nreal);

@@ -13,7 +13,7 @@ constexpr int kStages = 3;             // TMA pipeline depth
 constexpr int kStageFloats = 4096;     // 16 KB per stage
 constexpr int kSrcBlock = kStageFloats / 4;  // repulsion sources per stage (float4)
 constexpr int kMaxNx = kStageFloats;   // longest grid row a stage can hold
-constexpr float kEps2 = 1e-30f;        // added to every r^2 (zero-distance guard)
+constexpr float kEps2 = 1e-30f;        // smallest eps^2 added to every r^2 (zero-distance guard)
 
 // Device status bits (OR-ed into the context's status word).
 constexpr int kDevNonFinite = 1;
@@ -98,6 +98,7 @@ struct SymArgs {
     int64_t tiles;              // ceil(N / kTile)
     int64_t ctas;               // persistent CTAs; tri_count(tiles) units split evenly
     unsigned long long *acc;    // [N][NV] fixed-point sums (zeroed before the launch)
+    float eps2;                 // kernel sqrt(r^2 + eps^2): eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -112,6 +113,7 @@ struct AttrArgs {
     float hx;             // grid spacing along x (columns are x0 + q hx)
     Split sp;             // per_tile = ny*nz rows
     dacc4 *part;        // [tiles][slots][kTile] (x, y, z, energy)
+    float eps2;           // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -120,6 +122,7 @@ struct RepArgs {
     int64_t N;
     Split sp;             // per_tile = ceil(N / kSrcBlock) source blocks
     dacc4 *part;
+    float eps2;           // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -135,6 +138,7 @@ struct CombineArgs {
     double scale;         // G, A, R are multiplied by scale * (*scale_dev if set)
     const double *scale_dev;
     double2 *energy_blocks;  // energy mode: per-block (sum ea, sum er)
+    double eps;           // regularisation: the N self pairs (|d| = eps each) leave F^r
 };
 
 // Tile shapes of the pair kernels, chosen per problem by the autotuner
@@ -172,7 +176,7 @@ cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream
 
 // Fast attraction (field.cu): node field of a density and its interpolation.
 size_t field_bytes(int nx, int ny, int nz);
-cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, double hi,
+cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, double hi, double eps,
                         float4 *field, int sms, cudaStream_t st, const char **what);
 cudaError_t launch_interp(const float4 *pos, int64_t N, const float4 *field, int nx, int ny, int nz,
                           double lo, double hi, dacc4 *out, int sms, cudaStream_t st);
@@ -239,6 +243,7 @@ struct EngineArgs {
     unsigned int *queue;     // next item (reset to 0 before every launch)
     unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
     double *gstate;          // per-CTA projection state when it is not in shared memory
+    float eps2;              // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 

@@ -201,15 +201,16 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     aa.gxp = gxp; aa.ny = ny; aa.nz = nz; aa.rows_per_stage = kStageFloats / gxp;
     aa.hx = (float)((grid->hi - grid->lo) / nx);
     aa.x0 = grid->lo + 0.5 * ((grid->hi - grid->lo) / nx);
-    aa.sp = spa; aa.part = part_a; aa.status = status;
+    aa.sp = spa; aa.part = part_a; aa.status = status; aa.eps2 = kEps2;
     NA_CK(launch_attraction(aa, acc, false, kAttrDefault, st));
     RepArgs ra;
-    ra.pos = pos; ra.N = N; ra.sp = spr; ra.part = part_r; ra.status = status;
+    ra.pos = pos; ra.N = N; ra.sp = spr; ra.part = part_r; ra.status = status; ra.eps2 = kEps2;
     NA_CK(launch_repulsion(ra, acc, false, kRepDefault, st));
     CombineArgs cb;
     cb.N = N; cb.part_a = part_a; cb.part_r = part_r; cb.spa = spa; cb.spr = spr;
     cb.G = G; cb.A = nullptr; cb.R = nullptr; cb.G64 = nullptr;
     cb.scale = 1.0; cb.scale_dev = nullptr; cb.energy_blocks = nullptr; cb.racc = nullptr; cb.a_direct = nullptr;
+    cb.eps = 0.0;
     NA_CK(launch_combine(cb, G_dtype, sms, st));
     int h = 0;
     NA_CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));

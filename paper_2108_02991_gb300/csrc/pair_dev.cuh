@@ -70,7 +70,7 @@ constexpr int kAccBytes = kTile * 3 * 8;   // 24 KB per CTA: 3 values x 8 bytes 
 template <bool ENERGY, int NR, int T>
 __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const float *kxp,
                                           const float *ky, const float *kz, const float *yr,
-                                          const float *zr, float h, float (*st)[3])
+                                          const float *zr, float h, float eps2, float (*st)[3])
 {
     float s2[NR][T], sw[NR][T], sx[T];
 #pragma unroll
@@ -78,7 +78,7 @@ __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const floa
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const float dy = ky[t] - yr[r], dz = kz[t] - zr[r];
-            s2[r][t] = fmaf(dy, dy, fmaf(dz, dz, kEps2));
+            s2[r][t] = fmaf(dy, dy, fmaf(dz, dz, eps2));
             sw[r][t] = 0.f;
         }
         sx[t] = 0.f;
@@ -192,11 +192,11 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
             if (++iy == a.ny) { iy = 0; ++iz; }
             yr[1] = ys[iy]; zr[1] = zs[iz];
             if (++iy == a.ny) { iy = 0; ++iz; }
-            attr_rows<ENERGY, 2, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
+            attr_rows<ENERGY, 2, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
         }
         if (rr < nrows) {
             float yr[1] = {ys[iy]}, zr[1] = {zs[iz]};
-            attr_rows<ENERGY, 1, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, st);
+            attr_rows<ENERGY, 1, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
         }
 #pragma unroll
         for (int t = 0; t < T; ++t)
@@ -223,11 +223,11 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
 }
 
 template <bool ENERGY>
-__device__ __forceinline__ void rep_pair(float kx, float ky, float kz, const float4 q, float &rx,
-                                         float &ry, float &rz)
+__device__ __forceinline__ void rep_pair(float kx, float ky, float kz, const float4 q, float eps2,
+                                         float &rx, float &ry, float &rz)
 {
     const float dx = kx - q.x, dy = ky - q.y, dz = kz - q.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
     const float ri = rsqrt_sfu(r2);
     if (ENERGY) {
         rx = fmaf(r2, ri, rx);           // |d|
@@ -255,6 +255,7 @@ __device__ __forceinline__ bool repulsion_segment(const RepArgs &a, int64_t tile
     }
     SmemAcc<ACC, NT> acc(accbase, tid);
     acc.zero(T * NV);
+    const float eps2 = a.eps2;
     const uint32_t nst = (uint32_t)(b1 - b0);
     auto count_of = [&](int64_t b) -> int {
         const int64_t rem = a.N - b * kSrcBlock;
@@ -289,14 +290,14 @@ __device__ __forceinline__ bool repulsion_segment(const RepArgs &a, int64_t tile
                 const float4 q = buf[j];
 #pragma unroll
                 for (int t = 0; t < T; ++t)
-                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, rx[t], ry[t], rz[t]);
+                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, eps2, rx[t], ry[t], rz[t]);
             }
         } else {
             for (int j = 0; j < cnt; ++j) {
                 const float4 q = buf[j];
 #pragma unroll
                 for (int t = 0; t < T; ++t)
-                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, rx[t], ry[t], rz[t]);
+                    rep_pair<ENERGY>(kx[t], ky[t], kz[t], q, eps2, rx[t], ry[t], rz[t]);
             }
         }
 #pragma unroll

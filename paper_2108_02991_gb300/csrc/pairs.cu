@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_block_kernel(const Comb
 }
 
 __global__ void __launch_bounds__(kEnergyThreads) energy_final_kernel(const double2 *blocks, int nb,
-                                                                      int64_t N, double *out2)
+                                                                      int64_t N, double eps,
+                                                                      double *out2)
 {
     double ea = 0.0, er = 0.0;
     for (int b = threadIdx.x; b < nb; b += kEnergyThreads) {
@@ -199,7 +200,8 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_final_kernel(const doub
     if (threadIdx.x == 0) {
         const double n = (double)N;
         out2[0] = s.x / n;               // F^a
-        out2[1] = s.y / (2.0 * n * n);   // F^r
+        // the directed sums include the N self pairs, |0|_eps = eps each
+        out2[1] = (s.y - n * eps) / (2.0 * n * n);   // F^r
     }
 }
 
@@ -305,7 +307,7 @@ cudaError_t launch_combine_energy(const CombineArgs &c, double *out2, cudaStream
     energy_block_kernel<<<nb, kEnergyThreads, 0, st>>>(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    energy_final_kernel<<<1, kEnergyThreads, 0, st>>>(c.energy_blocks, nb, c.N, out2);
+    energy_final_kernel<<<1, kEnergyThreads, 0, st>>>(c.energy_blocks, nb, c.N, c.eps, out2);
     return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ void add_fix(unsigned long long *p, long long v)
 template <bool ENERGY, bool RAGGED, int S>
 __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const float *tx,
                                          const float *ty, const float *tz, const float *tm,
-                                         float (*ai)[3], float *jacc)
+                                         float eps2, float (*ai)[3], float *jacc)
 {
     constexpr int T = kSymT;
     constexpr int kSymChunk = 32 * S, kChunks = kTile / kSymChunk;
@@ -88,7 +88,7 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const float dx = tx[t] - sx[s], dy = ty[t] - sy[s], dz = tz[t] - sz[s];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
                     float ri = rsqrt_sfu(r2);
                     if (RAGGED) ri *= tm[t] * sm[s];
                     if (ENERGY) {
@@ -135,11 +135,13 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
 }
 
 // A diagonal item (I, I): the thread's targets against every source of the
-// tile, directed (each ordered pair once, target side only; the zero-distance
-// self term contributes nothing).
+// tile, directed (each ordered pair once, target side only; the self term
+// contributes nothing to the force and eps to the energy, which the energy
+// reduction removes).
 template <bool ENERGY>
 __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const float *tx,
-                                          const float *ty, const float *tz, float (*ai)[3])
+                                          const float *ty, const float *tz, float eps2,
+                                          float (*ai)[3])
 {
     constexpr int T = kSymT;
 #pragma unroll 2
@@ -148,7 +150,7 @@ __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const f
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const float dx = tx[t] - q.x, dy = ty[t] - q.y, dz = tz[t] - q.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kEps2)));
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
             const float ri = rsqrt_sfu(r2);
             if (ENERGY) {
                 ai[t][0] = fmaf(r2, ri, ai[t][0]);
@@ -243,14 +245,14 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
 #pragma unroll
         for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
         if (I == J) {
-            diag_item<ENERGY>(src, jvalid, tx, ty, tz, ai);
+            diag_item<ENERGY>(src, jvalid, tx, ty, tz, a.eps2, ai);
         } else {
             for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
             __syncthreads();
             if (jvalid < kTile)
-                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, a.eps2, ai, jacc);
             else
-                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, ai, jacc);
+                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, a.eps2, ai, jacc);
             for (int l = tid; l < jvalid; l += kSymThreads)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)

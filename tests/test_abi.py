@@ -139,6 +139,11 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert L.sparkling_attraction_field(h, None, None) == lib.E_INVAL
     assert L.sparkling_attraction_field(h, ctypes.byref(bad), None) == lib.E_INVAL
     assert L.sparkling_set_attraction(h, lib.ATTRACTION_DIRECT) == lib.OK
+    # regularised kernel
+    for eps in (-1.0, float("nan"), float("inf"), 1e4):
+        assert L.sparkling_set_regularisation(h, eps) == lib.E_INVAL, eps
+    assert L.sparkling_set_regularisation(h, 0.02) == lib.OK
+    assert L.sparkling_set_regularisation(h, 0.0) == lib.OK
     assert lib.sparkling_launch_count(ctx) == 0
     lib.sparkling_destroy(ctx)
 

@@ -259,3 +259,75 @@ def test_attraction_at_points_matches_forces_and_closed_form():
     d = pts - 0.1
     np.testing.assert_allclose(A1, d / np.linalg.norm(d, axis=1, keepdims=True), atol=1e-15)
     np.testing.assert_allclose(phi1, np.linalg.norm(d, axis=1), atol=1e-15)
+
+
+# --- regularised kernel H(r) = sqrt(r^2 + eps^2) (Sec. II-C, choice of step size)
+
+def test_regularised_two_samples_closed_form():
+    """N = 2 and one density cell: R_1 = (1/2) e / sqrt(|e|^2 + eps^2) = -R_2,
+    A_i = d_i / sqrt(|d_i|^2 + eps^2), F^r = 2 sqrt(|e|^2 + eps^2) / (2 N^2)."""
+    eps = 0.07
+    K = np.array([[0.1, -0.2, 0.05], [-0.15, 0.1, 0.2]])
+    grid = one_cell(0.0, 0.2)                    # cell centre (0.1, 0.1, 0.1)
+    A, R, G = oracle.forces(K, grid, eps=eps)
+    e = K[0] - K[1]
+    re = math.sqrt(e @ e + eps * eps)
+    np.testing.assert_allclose(R[0], 0.5 * e / re, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(R[1], -0.5 * e / re, rtol=0, atol=1e-16)
+    d = K - 0.1
+    rd = np.sqrt((d * d).sum(1) + eps * eps)
+    np.testing.assert_allclose(A, d / rd[:, None], rtol=0, atol=1e-16)
+    F, Fa, Fr = oracle.energy(K, grid, eps=eps)
+    assert Fr == pytest.approx(2 * re / 8, rel=1e-15)
+    assert Fa == pytest.approx(rd.sum() / 2, rel=1e-15)
+
+
+def test_regularised_coincident_samples_and_grid_point():
+    """With eps > 0 nothing is singular: two coincident samples repel with
+    zero force but add eps each to the directed distance sums (F^r = 2 eps /
+    (2 N^2) for N = 2), and a sample on a grid point adds rho eps to F^a."""
+    eps = 0.01
+    grid = one_cell(0.0, 0.2)
+    K = np.array([[0.1, 0.1, 0.1], [0.1, 0.1, 0.1]])
+    A, R, G = oracle.forces(K, grid, eps=eps)
+    np.testing.assert_array_equal(R, 0.0)
+    np.testing.assert_array_equal(A, 0.0)
+    F, Fa, Fr = oracle.energy(K, grid, eps=eps)
+    assert Fr == pytest.approx(2 * eps / 8, rel=1e-15)
+    assert Fa == pytest.approx(eps, rel=1e-15)
+
+
+def test_regularised_gradient_matches_central_differences():
+    """G / N is the derivative of the regularised energy, also at a pair of
+    coincident samples and at samples on grid points, where the plain norm
+    has a kink (h = 1e-6 against eps = 0.02: the energy is smooth there)."""
+    rng = np.random.default_rng(31)
+    grid = random_grid((4, 5, 3), seed=32)
+    eps = 0.02
+    N = 40
+    K = rng.uniform(-0.45, 0.45, size=(N, 3))
+    K[1] = K[0]                                  # coincident pair
+    K[2] = [-0.5 + 0.5 / 4, -0.5 + 1.5 / 5, -0.5 + 2.5 / 3]   # a grid point
+    _, _, G = oracle.forces(K, grid, eps=eps)
+    h = 1e-6
+    for i, c in [(0, 0), (1, 2), (2, 1), (2, 0)] + [(int(rng.integers(N)), int(rng.integers(3)))
+                                                    for _ in range(12)]:
+        Kp = K.copy(); Kp[i, c] += h
+        Km = K.copy(); Km[i, c] -= h
+        fd = (oracle.energy(Kp, grid, eps=eps)[0] - oracle.energy(Km, grid, eps=eps)[0]) / (2 * h)
+        assert fd == pytest.approx(G[i, c] / N, rel=1e-6, abs=1e-10)
+
+
+def test_regularised_tends_to_plain_norm():
+    """eps -> 0 recovers the plain kernel (no coincident points): the
+    difference of each unit-vector term is O(eps^2 / r^2)."""
+    p = inputs.make_problem("tiny")
+    A0, R0, G0 = oracle.forces(p.K, p.grid)
+    A1, R1, G1 = oracle.forces(p.K, p.grid, eps=1e-7)
+    assert np.abs(G1 - G0).max() < 1e-6
+    F0 = oracle.energy(p.K, p.grid)
+    F1 = oracle.energy(p.K, p.grid, eps=1e-7)
+    assert F1[0] == pytest.approx(F0[0], rel=1e-9)
+    # and eps changes the result visibly when it is not small
+    A2, _, _ = oracle.forces(p.K, p.grid, eps=0.05)
+    assert np.abs(A2 - A0).max() > 1e-3
