@@ -19,6 +19,13 @@ NumPy arrays.  See the C file for the definitions followed:
 * ``violation`` -- the constraint checker;
 * ``step``    -- one projected-gradient step (eq. proj_grad_descent).
 
+Algorithm 1 (multi-resolution SPARKLING):
+
+* ``upsample`` -- the linear interpolator L_{2d} between levels;
+* ``optimize`` -- n_git projected-gradient iterations at one resolution,
+  fixed step then Barzilai-Borwein (Sec. II-C, choice of step size);
+* ``multires`` -- the level loop with per-level constraint scaling.
+
 ``forces``, ``energy``, ``attraction_at`` and ``step`` take ``eps`` for the
 regularised kernel H(r) = sqrt(r^2 + eps^2) (Sec. II-C, choice of step size).
 """
@@ -65,6 +72,13 @@ def _load():
             lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64, d]
             lib.oracle_attraction_at.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p, d]
             lib.oracle_attraction_at.restype = ctypes.c_int
+            lib.oracle_upsample.argtypes = [p, i64, i64, p]
+            lib.oracle_optimize.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, i64, p,
+                                            i64, i64, i64, d, d, d, d, p]
+            lib.oracle_multires.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, i64, p,
+                                            i64, i64, i64, i64, d, d, d, d, d, d, p, p]
+            for f in (lib.oracle_upsample, lib.oracle_optimize, lib.oracle_multires):
+                f.restype = ctypes.c_int
             for f in (lib.oracle_forces, lib.oracle_energy, lib.oracle_project,
                       lib.oracle_violation, lib.oracle_step):
                 f.restype = ctypes.c_int
@@ -178,3 +192,62 @@ def step(K, Nc, Ns, grid, eta, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0
     if st != OK:
         raise ValueError(f"oracle_step failed ({st})")
     return K
+
+
+def upsample(K, Nc, d):
+    """L_{2d}: [Nc*d, 3] -> [Nc*2d, 3] (float64)."""
+    Kc = _f64(K).reshape(-1, 3)
+    if Kc.shape[0] != Nc * d:
+        raise ValueError("K must hold Nc*d samples")
+    out = np.empty((Nc * 2 * d, 3))
+    if _load().oracle_upsample(_ptr(Kc), Nc, d, _ptr(out)) != OK:
+        raise ValueError("oracle_upsample failed")
+    return out
+
+
+def optimize(K, Nc, Ns, grid, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0),
+             n_pit=100, n_git=10, n_fixed=20, eta=1e-3, eta_min=1e-12, eta_max=1e3, eps=0.0):
+    """n_git projected-gradient iterations at one resolution; returns
+    (K float64 [Nc*Ns, 3], steps [n_git])."""
+    Kw = _f64(K).reshape(-1, 3).copy()
+    if Kw.shape[0] != Nc * Ns:
+        raise ValueError("K must hold Nc*Ns samples")
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    pin_a = _f64(pin)
+    trace = np.zeros(max(n_git, 1))
+    st = _load().oracle_optimize(_ptr(Kw), Nc, Ns, _ptr(rho), nx, ny, nz, lo, hi, alpha, beta, box,
+                                 pin_index, _ptr(pin_a), n_pit, n_git, n_fixed, eta, eta_min,
+                                 eta_max, eps, _ptr(trace))
+    if st != OK:
+        raise ValueError(f"oracle_optimize failed ({st})")
+    return Kw, trace[:n_git]
+
+
+def multires(K, Nc, Ns, grid, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0, 0.0), n_pit=100,
+             start_level=0, n_git=10, n_fixed=20, eta=1e-3, eta_min=1e-12, eta_max=1e3,
+             alpha_factor=2.0, beta_factor=4.0, eps=0.0):
+    """Algorithm 1 from level start_level (K holds Nc * (Ns >> start_level)
+    samples) to the full resolution; returns (K [Nc*Ns, 3], [K of every
+    level before up-sampling], steps [levels, n_git])."""
+    Kc = _f64(K).reshape(-1, 3)
+    if Kc.shape[0] != Nc * (Ns >> start_level):
+        raise ValueError("K must hold Nc * (Ns >> start_level) samples")
+    Kw = np.zeros((Nc * Ns, 3))
+    Kw[:Kc.shape[0]] = Kc
+    levels = list(range(start_level, -1, -1))
+    sizes = [Nc * (Ns >> l) for l in levels]
+    lev = np.zeros((sum(sizes), 3))
+    trace = np.zeros((len(levels), max(n_git, 1)))
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    pin_a = _f64(pin)
+    st = _load().oracle_multires(_ptr(Kw), Nc, Ns, _ptr(rho), nx, ny, nz, lo, hi, alpha, beta, box,
+                                 pin_index, _ptr(pin_a), n_pit, start_level, n_git, n_fixed, eta,
+                                 eta_min, eta_max, alpha_factor, beta_factor, eps, _ptr(lev),
+                                 _ptr(trace))
+    if st != OK:
+        raise ValueError(f"oracle_multires failed ({st})")
+    out, o = [], 0
+    for n in sizes:
+        out.append(lev[o:o + n].copy())
+        o += n
+    return Kw, out, trace[:, :n_git]

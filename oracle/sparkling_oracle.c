@@ -424,3 +424,138 @@ int oracle_step(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_t nx
     free(G);
     return st;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Multi-resolution driver (Algorithm 1, Secs. II-C "choice of step size",  */
+/* II-E "multi-resolution strategy" and "overall algorithm").               */
+
+/* The linear interpolator L_{2d}: a shot of d samples (time 2n on the fine
+ * raster) becomes 2d samples at times m = 0 .. 2d-1: even samples are the
+ * coarse ones, odd samples the midpoints of consecutive coarse samples, and
+ * the last one continues the last coarse segment (linear extrapolation).
+ * A one-sample shot is repeated.  Kc [Nc][d][3] -> Kf [Nc][2d][3]. */
+int oracle_upsample(const double *Kc, int64_t Nc, int64_t d, double *Kf)
+{
+    if (!Kc || !Kf || Nc < 0 || d < 1)
+        return ORACLE_EINVAL;
+    for (int64_t s = 0; s < Nc; ++s) {
+        const double *c = Kc + 3 * d * s;
+        double *f = Kf + 6 * d * s;
+        for (int64_t n = 0; n < d; ++n)
+            for (int a = 0; a < 3; ++a) {
+                double here = c[3 * n + a];
+                double next;
+                if (n + 1 < d)
+                    next = 0.5 * (here + c[3 * (n + 1) + a]);
+                else if (d > 1)
+                    next = here + 0.5 * (here - c[3 * (n - 1) + a]);
+                else
+                    next = here;
+                f[6 * n + a] = here;
+                f[6 * n + 3 + a] = next;
+            }
+    }
+    return ORACLE_OK;
+}
+
+/* n_git projected-gradient iterations at one resolution (the inner loop of
+ * Algorithm 1, eq. proj_grad_descent): K <- Pi(K - eta_t G(K)) with the
+ * fixed step eta for the first n_fixed iterations and the Barzilai-Borwein
+ * step eta_t = <s, s> / <s, y> afterwards, s = K_t - K_{t-1} and
+ * y = G(K_t) - G(K_{t-1}) (G = N dF/dK, so eta stays in G units).  When
+ * <s, y> <= 0 the previous step is kept; every BB step is clamped to
+ * [eta_min, eta_max].  trace[t] (optional) receives the step of iteration t.
+ * K [Nc*Ns][3] is updated in place. */
+int oracle_optimize(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_t nx, int64_t ny,
+                    int64_t nz, double lo, double hi, double alpha, double beta, double box,
+                    int64_t pin_index, const double *pin, int64_t n_pit, int64_t n_git,
+                    int64_t n_fixed, double eta, double eta_min, double eta_max, double eps,
+                    double *trace)
+{
+    const int64_t N = Nc * Ns;
+    if (!K || Nc < 1 || Ns < 1 || N < 2 || n_git < 0 || n_fixed < 0 || !(eta_min > 0) ||
+        !(eta_max >= eta_min))
+        return ORACLE_EINVAL;
+    double *G = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    double *Kp = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    double *Gp = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    double *half = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    int st = (G && Kp && Gp && half) ? ORACLE_OK : ORACLE_EINVAL;
+    double step = eta;
+    for (int64_t t = 0; t < n_git && st == ORACLE_OK; ++t) {
+        st = oracle_forces(K, N, rho, nx, ny, nz, lo, hi, NULL, N, NULL, NULL, G, NULL, NULL, eps);
+        if (st != ORACLE_OK)
+            break;
+        if (t < n_fixed) {
+            step = eta;
+        } else if (t > 0) {
+            double ss = 0.0, sy = 0.0;
+            for (int64_t m = 0; m < 3 * N; ++m) {
+                double s = K[m] - Kp[m], y = G[m] - Gp[m];
+                ss += s * s;
+                sy += s * y;
+            }
+            if (sy > 0.0 && isfinite(ss / sy)) {
+                step = ss / sy;
+                if (step < eta_min) step = eta_min;
+                if (step > eta_max) step = eta_max;
+            }
+        }
+        if (trace)
+            trace[t] = step;
+        for (int64_t m = 0; m < 3 * N; ++m) {
+            Kp[m] = K[m];
+            Gp[m] = G[m];
+            half[m] = K[m] - step * G[m];
+        }
+        st = oracle_project(half, K, Nc, Ns, alpha, beta, box, pin_index, pin, n_pit, 0.0, 0.0, 0,
+                            NULL);
+    }
+    free(G); free(Kp); free(Gp); free(half);
+    return st;
+}
+
+/* Algorithm 1: levels l = start_level .. 0, level l with Ns / 2^l samples
+ * per shot, per-step constraints alpha * alpha_factor^l and
+ * beta * beta_factor^l, the pinned sample pin_index / 2^l (floor), n_git
+ * iterations of oracle_optimize, then L_{2d} up to the next level.  K holds
+ * Nc * (Ns >> start_level) samples on entry and Nc * Ns on exit (its buffer
+ * is sized for Nc * Ns).  levels_out (optional) receives the result of
+ * every level before up-sampling, level after level; trace (optional) the
+ * steps, n_git per level. */
+int oracle_multires(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_t nx, int64_t ny,
+                    int64_t nz, double lo, double hi, double alpha, double beta, double box,
+                    int64_t pin_index, const double *pin, int64_t n_pit, int64_t start_level,
+                    int64_t n_git, int64_t n_fixed, double eta, double eta_min, double eta_max,
+                    double alpha_factor, double beta_factor, double eps, double *levels_out,
+                    double *trace)
+{
+    if (!K || Nc < 1 || start_level < 0 || start_level > 30 || (Ns % ((int64_t)1 << start_level)))
+        return ORACLE_EINVAL;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(3 * Nc * Ns));
+    if (!tmp)
+        return ORACLE_EINVAL;
+    int st = ORACLE_OK;
+    for (int64_t l = start_level; l >= 0 && st == ORACLE_OK; --l) {
+        const int64_t Nsl = Ns >> l;
+        const double al = alpha * pow(alpha_factor, (double)l);
+        const double bl = beta * pow(beta_factor, (double)l);
+        const int64_t pl = pin_index >= 0 ? pin_index >> l : -1;
+        st = oracle_optimize(K, Nc, Nsl, rho, nx, ny, nz, lo, hi, al, bl, box, pl, pin, n_pit,
+                             n_git, n_fixed, eta, eta_min, eta_max, eps, trace);
+        if (st != ORACLE_OK)
+            break;
+        if (levels_out) {
+            memcpy(levels_out, K, sizeof(double) * (size_t)(3 * Nc * Nsl));
+            levels_out += 3 * Nc * Nsl;
+        }
+        if (trace)
+            trace += n_git;
+        if (l > 0) {
+            st = oracle_upsample(K, Nc, Nsl, tmp);
+            memcpy(K, tmp, sizeof(double) * (size_t)(6 * Nc * Nsl));
+        }
+    }
+    free(tmp);
+    return st;
+}
