@@ -65,6 +65,7 @@ extern "C" {
 #define SPARKLING_E_NONFINITE 4 /* NaN/Inf in K or rho, or negative rho */
 #define SPARKLING_E_TIMEOUT 5   /* a bounded device wait gave up (the kernel returned early) */
 #define SPARKLING_E_NOTCONV 6   /* converged-mode projection did not certify within n_iter */
+#define SPARKLING_E_IO 7        /* a checkpoint file could not be written */
 
 /* Element types of K, G, A, R. */
 #define SPARKLING_F32 0
@@ -118,7 +119,8 @@ typedef struct sparkling_proj {
 #define SPARKLING_KERNEL_COMBINE 3
 #define SPARKLING_KERNEL_PROJECT 4
 #define SPARKLING_KERNEL_ENGINE 5   /* a whole batched step (packs + persistent engine) */
-#define SPARKLING_KERNEL_COUNT 6
+#define SPARKLING_KERNEL_DRIVER 6   /* up-sampling and step-size reductions of the driver */
+#define SPARKLING_KERNEL_COUNT 7
 
 /* How the attraction term is evaluated (sparkling_set_attraction). */
 #define SPARKLING_ATTRACTION_DIRECT 0   /* direct sum over the grid: O(N P) */
@@ -126,6 +128,19 @@ typedef struct sparkling_proj {
 
 /* Flags of sparkling_step_batched. */
 #define SPARKLING_BATCH_GRAPH 1     /* replay the step from a cached CUDA graph */
+
+/* Step schedule of the multi-resolution driver (Algorithm 1 and Sec. II-C,
+ * choice of step size). */
+typedef struct sparkling_schedule {
+    double eta;            /* fixed step, in units of G (K <- Pi(K - eta G)); > 0 */
+    double eta_min;        /* Barzilai-Borwein steps are clamped to [eta_min, eta_max], */
+    double eta_max;        /*   0 < eta_min <= eta_max */
+    double alpha_factor;   /* level l runs under alpha * alpha_factor^l and beta * beta_factor^l */
+    double beta_factor;    /*   (per-step bounds: 2 and 4 when the raster step doubles) */
+    int32_t n_git;         /* projected-gradient iterations per level, >= 0 */
+    int32_t n_fixed;       /* iterations on the fixed step before Barzilai-Borwein (the paper: 20) */
+    int32_t reserved[2];
+} sparkling_schedule;
 
 /* Create a context bound to CUDA device `device`.  Nothing is allocated on
  * the device and no CUDA call is made until the first compute call.
@@ -332,6 +347,58 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
  * SPARKLING_E_NOMEM, SPARKLING_E_CUDA (CUDA or cuFFT failure). */
 SPARKLING_API int sparkling_attraction_field(sparkling_ctx *ctx, const sparkling_grid *grid,
                                              void *stream);
+
+/* The linear interpolator between resolution levels of Algorithm 1
+ * (L_{2d}, Sec. II-E): every shot of d samples becomes 2d samples -- sample
+ * n goes to 2n, sample 2n+1 is the midpoint of samples n and n+1, and the
+ * last one continues the last segment (a one-sample shot is repeated).
+ *   Kc  device [Nc*d][3] of dtype (read only); Kf device [Nc*2d][3] of dtype
+ *   (must not overlap Kc).  Arithmetic in double, one rounding to dtype.
+ * Asynchronous on `stream`. */
+SPARKLING_API int sparkling_upsample(sparkling_ctx *ctx, const void *Kc, void *Kf, int dtype,
+                                     int64_t Nc, int64_t d, void *stream);
+
+/* n_git projected-gradient iterations at one resolution (the inner loop of
+ * Algorithm 1, eq. proj_grad_descent): K <- Pi_Q(K - eta_t G(K)), where
+ * eta_t = sched->eta for the first sched->n_fixed iterations and then the
+ * Barzilai-Borwein step eta_t = <s, s> / <s, y>, s = K_t - K_{t-1},
+ * y = G(K_t) - G(K_{t-1}) (FP64 reductions on the device), clamped to
+ * [eta_min, eta_max]; when <s, y> <= 0 the previous step is kept.
+ *   K      device [Nc*Ns][3] of K_dtype, updated in place
+ *   proj   constraint set of this resolution (tol <= 0: n_iter FISTA steps)
+ *   trace  optional host [n_git]: the step of every iteration
+ * Uses the context's attraction mode and regularisation.  Blocks on
+ * `stream` (the step is read back after each gradient once Barzilai-Borwein
+ * is on); device errors are returned. */
+SPARKLING_API int sparkling_optimize(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc,
+                                     int64_t Ns, const sparkling_grid *grid,
+                                     const sparkling_proj *proj, int acc,
+                                     const sparkling_schedule *sched, double *trace, void *stream);
+
+/* Algorithm 1, the multi-resolution SPARKLING: levels l = start_level, ..., 0,
+ * level l with Ns / 2^l samples per shot, constraints
+ * alpha * alpha_factor^l, beta * beta_factor^l and the pinned sample
+ * pin_index / 2^l (floor), n_git iterations of sparkling_optimize, then
+ * sparkling_upsample to the next level.  Level 0 is optimised as well
+ * (the printed loop stops after the last up-sampling).
+ *   K      device buffer of Nc*Ns*3 elements of K_dtype; holds
+ *          Nc * (Ns >> start_level) samples on entry, Nc * Ns on exit
+ *   proj   the full-resolution constraint set
+ *   checkpoint_prefix  NULL, or a path prefix: after each level the result
+ *          (before up-sampling) is written to "<prefix>_level<l>.bin" -- a
+ *          64-byte header ("SPKLCKPT", int64 version 1, Nc, samples per
+ *          shot, level, K_dtype, 16 reserved bytes) and the raw [Nc*Ns_l][3]
+ *          array; resume with sparkling_upsample of a checkpoint and
+ *          start_level = l - 1
+ *   trace  optional host [(start_level + 1) * n_git] steps, level by level
+ * Ns must be a multiple of 2^start_level and Ns >> start_level >= 1.
+ * Blocks; errors as sparkling_optimize, SPARKLING_E_IO for a checkpoint
+ * that cannot be written. */
+SPARKLING_API int sparkling_multires(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc,
+                                     int64_t Ns, const sparkling_grid *grid,
+                                     const sparkling_proj *proj, int acc,
+                                     const sparkling_schedule *sched, int32_t start_level,
+                                     const char *checkpoint_prefix, double *trace, void *stream);
 
 /* Number of kernels this context has launched since it was created. */
 SPARKLING_API int64_t sparkling_launch_count(const sparkling_ctx *ctx);

@@ -15,10 +15,10 @@ from typing import Optional, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsparkling.so")
 
-OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV = range(7)
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV, E_IO = range(8)
 F32, F64 = 0, 1
 ACC_KAHAN32, ACC_FP64 = 0, 1
-KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine")
+KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine", "driver")
 BATCH_GRAPH = 1
 ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
 
@@ -30,6 +30,7 @@ ABI_SYMBOLS = (
     "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
     "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
+    "sparkling_upsample", "sparkling_optimize", "sparkling_multires",
 )
 
 
@@ -52,6 +53,23 @@ class Proj(ctypes.Structure):
                 ("pin", ctypes.c_double * 3), ("pin_index", ctypes.c_int32),
                 ("n_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Schedule(ctypes.Structure):
+    """sparkling_schedule: step schedule and level scaling of the driver."""
+    _fields_ = [("eta", ctypes.c_double), ("eta_min", ctypes.c_double),
+                ("eta_max", ctypes.c_double), ("alpha_factor", ctypes.c_double),
+                ("beta_factor", ctypes.c_double), ("n_git", ctypes.c_int32),
+                ("n_fixed", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+def make_schedule(eta, n_git, n_fixed=20, eta_min=1e-12, eta_max=1e3, alpha_factor=2.0,
+                  beta_factor=4.0) -> Schedule:
+    sc = Schedule()
+    sc.eta, sc.eta_min, sc.eta_max = float(eta), float(eta_min), float(eta_max)
+    sc.alpha_factor, sc.beta_factor = float(alpha_factor), float(beta_factor)
+    sc.n_git, sc.n_fixed = int(n_git), int(n_fixed)
+    return sc
 
 
 _lib_handle = None
@@ -89,6 +107,10 @@ def lib() -> ctypes.CDLL:
             "sparkling_set_attraction": ([p, i], i),
             "sparkling_attraction_field": ([p, p, p], i),
             "sparkling_set_regularisation": ([p, ctypes.c_double], i),
+            "sparkling_upsample": ([p, p, p, i, i64, i64, p], i),
+            "sparkling_optimize": ([p, p, i, i64, i64, p, p, i, p, p, p], i),
+            "sparkling_multires": ([p, p, i, i64, i64, p, p, i, p, ctypes.c_int32, ctypes.c_char_p,
+                                    p, p], i),
             "sparkling_step_batched": ([p, ctypes.c_int32, p, p, i, ctypes.c_int32,
                                         ctypes.POINTER(Grid), p, ctypes.POINTER(Proj), i, i, p], i),
         }
@@ -352,6 +374,58 @@ def sparkling_attraction_field(ctx: Context, grid: Grid, stream=None) -> None:
     """(Re)build the node field of grid's density (blocking)."""
     _check(ctx, lib().sparkling_attraction_field(ctx.handle, ctypes.byref(grid),
                                                  _stream(stream)))
+
+
+def sparkling_upsample(ctx: Context, Kc, Nc: int, d: int, Kf=None, stream=None):
+    """L_{2d} between levels: [Nc*d, 3] -> [Nc*2d, 3] (a new tensor unless Kf)."""
+    import torch
+    if Kf is None:
+        Kf = torch.empty(Nc * 2 * d, 3, dtype=Kc.dtype, device=Kc.device)
+    _check(ctx, lib().sparkling_upsample(ctx.handle, _dev_ptr(Kc, "Kc"), _dev_ptr(Kf, "Kf"),
+                                         _dtype_code(Kc), int(Nc), int(d), _stream(stream)))
+    return Kf
+
+
+def sparkling_optimize(ctx: Context, K, Nc: int, Ns: int, grid: Grid, proj: Proj,
+                       sched: Schedule, acc: int = ACC_KAHAN32, stream=None):
+    """n_git projected-gradient iterations (fixed step, then Barzilai-Borwein)
+    on K in place; returns the list of steps."""
+    trace = (ctypes.c_double * max(sched.n_git, 1))()
+    _check(ctx, lib().sparkling_optimize(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), int(Nc),
+                                         int(Ns), ctypes.byref(grid), ctypes.byref(proj), acc,
+                                         ctypes.byref(sched), trace, _stream(stream)))
+    return list(trace)[:sched.n_git]
+
+
+def sparkling_multires(ctx: Context, K, Nc: int, Ns: int, grid: Grid, proj: Proj,
+                       sched: Schedule, start_level: int, acc: int = ACC_KAHAN32,
+                       checkpoint_prefix: Optional[str] = None, stream=None):
+    """Algorithm 1 from level start_level to the full resolution.  K is a
+    buffer of Nc*Ns rows whose first Nc*(Ns >> start_level) rows hold the
+    initial pattern; returns the steps [levels][n_git]."""
+    levels = start_level + 1
+    trace = (ctypes.c_double * max(levels * sched.n_git, 1))()
+    pre = checkpoint_prefix.encode() if checkpoint_prefix else None
+    _check(ctx, lib().sparkling_multires(ctx.handle, _dev_ptr(K, "K"), _dtype_code(K), int(Nc),
+                                         int(Ns), ctypes.byref(grid), ctypes.byref(proj), acc,
+                                         ctypes.byref(sched), int(start_level), pre, trace,
+                                         _stream(stream)))
+    n = sched.n_git
+    return [list(trace)[l * n:(l + 1) * n] for l in range(levels)]
+
+
+def read_checkpoint(path: str):
+    """(level, Nc, samples per shot, numpy array [Nc*Ns_l, 3]) of a checkpoint file."""
+    import numpy as np
+    with open(path, "rb") as f:
+        head = f.read(64)
+        if head[:8] != b"SPKLCKPT":
+            raise ValueError(f"{path} is not a checkpoint")
+        version, nc, ns, level, dtype = np.frombuffer(head[8:48], dtype=np.int64)
+        if version != 1:
+            raise ValueError(f"unknown checkpoint version {version}")
+        arr = np.frombuffer(f.read(), dtype=np.float32 if dtype == F32 else np.float64)
+    return int(level), int(nc), int(ns), arr.reshape(-1, 3).copy()
 
 
 def sparkling_launch_count(ctx: Context) -> int:

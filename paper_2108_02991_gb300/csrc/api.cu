@@ -1090,6 +1090,193 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
     return SPARKLING_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-resolution driver (Algorithm 1).
+
+namespace {
+
+int validate_schedule(sparkling_ctx *ctx, const sparkling_schedule *sc)
+{
+    if (!sc) return fail(ctx, SPARKLING_E_INVAL, "sched is NULL");
+    if (!(sc->eta > 0) || !std::isfinite(sc->eta))
+        return fail(ctx, SPARKLING_E_INVAL, "sched->eta must be finite and > 0");
+    if (!(sc->eta_min > 0) || !(sc->eta_max >= sc->eta_min) || std::isnan(sc->eta_max))
+        return fail(ctx, SPARKLING_E_INVAL, "sched needs 0 < eta_min <= eta_max");
+    if (!(sc->alpha_factor > 0) || !(sc->beta_factor > 0) || !std::isfinite(sc->alpha_factor) ||
+        !std::isfinite(sc->beta_factor))
+        return fail(ctx, SPARKLING_E_INVAL, "sched alpha_factor, beta_factor must be finite and > 0");
+    if (sc->n_git < 0 || sc->n_fixed < 0)
+        return fail(ctx, SPARKLING_E_INVAL, "sched n_git, n_fixed must be >= 0");
+    return SPARKLING_OK;
+}
+
+int optimize_checks(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns,
+                    const sparkling_grid *grid, const sparkling_proj *proj, int acc,
+                    const sparkling_schedule *sc)
+{
+    int s;
+    if ((s = check_shots(ctx, Nc, Ns))) return s;
+    if ((s = common_checks(ctx, K, K_dtype, Nc * Ns, grid, acc))) return s;
+    if ((s = validate_proj(ctx, proj, Ns))) return s;
+    return validate_schedule(ctx, sc);
+}
+
+// The iterations of sparkling_optimize (arguments already validated).
+int run_optimize(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns,
+                 const sparkling_grid *grid, const sparkling_proj *proj, int acc,
+                 const sparkling_schedule *sc, double *trace, cudaStream_t st)
+{
+    const int64_t N = Nc * Ns, n3 = 3 * N;
+    PairPlan P;
+    Carve cv;
+    int s;
+    if ((s = plan_pairs(ctx, N, grid, acc, false, true, P, cv))) return s;
+    ProjPlan L;
+    if ((s = plan_project(ctx, K_dtype, Nc, Ns, cv, L))) return s;
+    const size_t o_kp = cv.take((size_t)n3 * sizeof(double));
+    const size_t o_gp = cv.take((size_t)n3 * sizeof(double));
+    const size_t o_part = cv.take((size_t)bb_blocks(n3, ctx->sms) * sizeof(double2));
+    if ((s = ensure_ws(ctx, cv.off))) return s;
+    const double *G64 = at<double>(ctx, P.o_g64);
+    double step = sc->eta;
+    for (int t = 0; t < sc->n_git; ++t) {
+        if ((s = run_pairs(ctx, K, K_dtype, grid, acc, false, P, nullptr, K_dtype, nullptr, nullptr,
+                           true, st)))
+            return s;
+        const bool bb = t >= sc->n_fixed && t > 0;
+        {
+            LaunchScope ls(ctx, SPARKLING_KERNEL_DRIVER, st);
+            CK(launch_bb(K, K_dtype, at<double>(ctx, o_kp), G64, at<double>(ctx, o_gp), n3, bb,
+                         at<double2>(ctx, o_part), ctx->d_small + 2, ctx->sms, st));
+            ls.done(bb ? 2 : 1);
+        }
+        if (t < sc->n_fixed) {
+            step = sc->eta;
+        } else if (bb) {
+            double h[2];
+            CK(cudaMemcpyAsync(h, ctx->d_small + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            if ((s = read_status(ctx, st))) return s;
+            if (h[1] > 0.0 && std::isfinite(h[0] / h[1]))
+                step = std::min(std::max(h[0] / h[1], sc->eta_min), sc->eta_max);
+        }
+        if (trace) trace[t] = step;
+        if ((s = run_project(ctx, K, K_dtype, Nc, Ns, proj, G64, step, L, false, st))) return s;
+        if (proj->tol > 0 && (s = finish_project(ctx, proj, nullptr, st))) return s;
+    }
+    return read_status(ctx, st);
+}
+
+int write_checkpoint(sparkling_ctx *ctx, const char *prefix, int level, const void *K, int K_dtype,
+                     int64_t Nc, int64_t Ns, cudaStream_t st)
+{
+    const size_t bytes = (size_t)Nc * Ns * 3 * (K_dtype == SPARKLING_F32 ? 4 : 8);
+    std::vector<char> host(bytes);
+    CK(cudaMemcpyAsync(host.data(), K, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    char path[4096];
+    if (snprintf(path, sizeof path, "%s_level%d.bin", prefix, level) >= (int)sizeof path)
+        return fail(ctx, SPARKLING_E_IO, "checkpoint path too long");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, SPARKLING_E_IO, "cannot open %s for writing", path);
+    char head[64] = {0};
+    std::memcpy(head, "SPKLCKPT", 8);
+    const int64_t fields[5] = {1, Nc, Ns, level, K_dtype};
+    std::memcpy(head + 8, fields, sizeof fields);
+    bool ok = std::fwrite(head, 1, sizeof head, f) == sizeof head &&
+              std::fwrite(host.data(), 1, bytes, f) == bytes;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, SPARKLING_E_IO, "writing %s failed", path);
+    return SPARKLING_OK;
+}
+
+} // namespace
+
+SPARKLING_API int sparkling_upsample(sparkling_ctx *ctx, const void *Kc, void *Kf, int dtype,
+                                     int64_t Nc, int64_t d, void *stream)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    int s;
+    if (!Kc || !Kf) return fail(ctx, SPARKLING_E_INVAL, "Kc and Kf are required");
+    if ((s = validate_dtype(ctx, dtype, "K"))) return s;
+    if (Nc < 1 || d < 1 || Nc > ((int64_t)1 << 40) / d)
+        return fail(ctx, SPARKLING_E_INVAL, "Nc = %lld, d = %lld out of range", (long long)Nc,
+                    (long long)d);
+    const size_t es = dtype == SPARKLING_F32 ? 4 : 8;
+    const char *a = static_cast<const char *>(Kc), *b = static_cast<const char *>(Kf);
+    if (a < b + (size_t)Nc * 2 * d * 3 * es && b < a + (size_t)Nc * d * 3 * es)
+        return fail(ctx, SPARKLING_E_INVAL, "Kc and Kf overlap");
+    if ((s = lazy_init(ctx))) return s;
+    if (!is_device_ptr(Kc) || !is_device_ptr(Kf))
+        return fail(ctx, SPARKLING_E_INVAL, "Kc and Kf must be device memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaunchScope ls(ctx, SPARKLING_KERNEL_DRIVER, st);
+    CK(launch_upsample(Kc, Kf, dtype, Nc, d, ctx->sms, st));
+    ls.done();
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_optimize(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc,
+                                     int64_t Ns, const sparkling_grid *grid,
+                                     const sparkling_proj *proj, int acc,
+                                     const sparkling_schedule *sched, double *trace, void *stream)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    int s;
+    if ((s = optimize_checks(ctx, K, K_dtype, Nc, Ns, grid, proj, acc, sched))) return s;
+    if ((s = lazy_init(ctx))) return s;
+    if (!is_device_ptr(K) || !is_device_ptr(grid->rho))
+        return fail(ctx, SPARKLING_E_INVAL, "K and grid->rho must be device memory");
+    return run_optimize(ctx, K, K_dtype, Nc, Ns, grid, proj, acc, sched, trace,
+                        static_cast<cudaStream_t>(stream));
+}
+
+SPARKLING_API int sparkling_multires(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc,
+                                     int64_t Ns, const sparkling_grid *grid,
+                                     const sparkling_proj *proj, int acc,
+                                     const sparkling_schedule *sched, int32_t start_level,
+                                     const char *checkpoint_prefix, double *trace, void *stream)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    int s;
+    if (start_level < 0 || start_level > 20 || Ns % ((int64_t)1 << start_level) != 0)
+        return fail(ctx, SPARKLING_E_INVAL, "Ns = %lld must be a multiple of 2^start_level (%d)",
+                    (long long)Ns, start_level);
+    if ((s = optimize_checks(ctx, K, K_dtype, Nc, Ns, grid, proj, acc, sched))) return s;
+    if ((s = check_shots(ctx, Nc, Ns >> start_level))) return s;
+    if (Nc * (Ns >> start_level) < 2)
+        return fail(ctx, SPARKLING_E_INVAL, "the first level needs at least 2 samples");
+    if ((s = lazy_init(ctx))) return s;
+    if (!is_device_ptr(K) || !is_device_ptr(grid->rho))
+        return fail(ctx, SPARKLING_E_INVAL, "K and grid->rho must be device memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = K_dtype == SPARKLING_F32 ? 4 : 8;
+    for (int l = start_level; l >= 0; --l) {
+        const int64_t Nsl = Ns >> l;
+        sparkling_proj pl = *proj;
+        pl.alpha = proj->alpha * std::pow(sched->alpha_factor, (double)l);
+        pl.beta = proj->beta * std::pow(sched->beta_factor, (double)l);
+        pl.pin_index = proj->pin_index >= 0 ? proj->pin_index >> l : -1;
+        if ((s = run_optimize(ctx, K, K_dtype, Nc, Nsl, grid, &pl, acc, sched, trace, st))) return s;
+        if (trace) trace += sched->n_git;
+        if (checkpoint_prefix &&
+            (s = write_checkpoint(ctx, checkpoint_prefix, l, K, K_dtype, Nc, Nsl, st)))
+            return s;
+        if (l > 0) {
+            Carve cv;
+            const size_t o_up = cv.take((size_t)Nc * 2 * Nsl * 3 * es);
+            if ((s = ensure_ws(ctx, cv.off))) return s;
+            void *tmp = at<char>(ctx, o_up);
+            {
+                LaunchScope ls(ctx, SPARKLING_KERNEL_DRIVER, st);
+                CK(launch_upsample(K, tmp, K_dtype, Nc, Nsl, ctx->sms, st));
+                ls.done();
+            }
+            CK(cudaMemcpyAsync(K, tmp, (size_t)Nc * 2 * Nsl * 3 * es, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return read_status(ctx, st);
+}
+
 SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const int64_t *traj_off,
                                          void *K, int K_dtype, int32_t Ns,
                                          const sparkling_grid *grids, const double *eta,

@@ -181,6 +181,13 @@ cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, dou
 cudaError_t launch_interp(const float4 *pos, int64_t N, const float4 *field, int nx, int ny, int nz,
                           double lo, double hi, dacc4 *out, int sms, cudaStream_t st);
 
+// Multi-resolution driver (driver.cu).  dtype: 0 float, 1 double.
+cudaError_t launch_upsample(const void *Kc, void *Kf, int dtype, int64_t Nc, int64_t d, int sms,
+                            cudaStream_t st);
+int bb_blocks(int64_t n, int sms);
+cudaError_t launch_bb(const void *K, int dtype, double *Kp, const double *G, double *Gp, int64_t n,
+                      bool dots, double2 *part, double *out, int sms, cudaStream_t st);
+
 // Projection (project.cu).
 struct ProjArgs {
     void *K;               // [Nc*Ns][3] in/out

@@ -49,17 +49,20 @@ def test_struct_layout_matches_c(lib, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sparkling.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sparkling_grid), offsetof(sparkling_grid, n), sizeof(sparkling_proj),"
         "offsetof(sparkling_proj, pin), offsetof(sparkling_proj, pin_index),"
         "offsetof(sparkling_proj, n_iter), offsetof(sparkling_proj, check_every),"
-        "offsetof(sparkling_grid, hi));return 0;}\n")
+        "offsetof(sparkling_grid, hi), sizeof(sparkling_schedule),"
+        "offsetof(sparkling_schedule, n_git), offsetof(sparkling_schedule, beta_factor));"
+        "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    G, P = lib.Grid, lib.Proj
+    G, P, S = lib.Grid, lib.Proj, lib.Schedule
     want = [ctypes.sizeof(G), G.n.offset, ctypes.sizeof(P), P.pin.offset, P.pin_index.offset,
-            P.n_iter.offset, P.check_every.offset, G.hi.offset]
+            P.n_iter.offset, P.check_every.offset, G.hi.offset, ctypes.sizeof(S), S.n_git.offset,
+            S.beta_factor.offset]
     assert got == want
 
 
@@ -144,6 +147,26 @@ def test_argument_validation_before_any_cuda_call(lib):
         assert L.sparkling_set_regularisation(h, eps) == lib.E_INVAL, eps
     assert L.sparkling_set_regularisation(h, 0.02) == lib.OK
     assert L.sparkling_set_regularisation(h, 0.0) == lib.OK
+    # driver: schedule and level checks
+    def opt(sc, Nc=4, Ns=8):
+        return L.sparkling_optimize(h, dummy, 0, Nc, Ns, ctypes.byref(g), ctypes.byref(p), 0,
+                                    ctypes.byref(sc) if sc is not None else None, None, None)
+    assert opt(None) == lib.E_INVAL
+    for field, value in (("eta", 0.0), ("eta", float("inf")), ("eta_min", 0.0),
+                         ("eta_max", 1e-20), ("alpha_factor", -2.0), ("n_git", -1),
+                         ("n_fixed", -3)):
+        sc = lib.make_schedule(1e-3, 10)
+        setattr(sc, field, value)
+        assert opt(sc) == lib.E_INVAL, field
+    sc = lib.make_schedule(1e-3, 10)
+    def multi(start, Ns=64):
+        return L.sparkling_multires(h, dummy, 0, 4, Ns, ctypes.byref(g), ctypes.byref(p), 0,
+                                    ctypes.byref(sc), start, None, None, None)
+    assert multi(-1) == lib.E_INVAL
+    assert multi(3, Ns=36) == lib.E_INVAL          # 36 is not a multiple of 8
+    assert L.sparkling_upsample(h, dummy, dummy, 0, 4, 8, None) == lib.E_INVAL   # overlap
+    assert L.sparkling_upsample(h, dummy, None, 0, 4, 8, None) == lib.E_INVAL
+    assert L.sparkling_upsample(h, dummy, ctypes.c_void_p(0x100000), 0, 0, 8, None) == lib.E_INVAL
     assert lib.sparkling_launch_count(ctx) == 0
     lib.sparkling_destroy(ctx)
 
