@@ -441,9 +441,9 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
         // a sub-triangle of about 1e11 directed pairs (the first tt tiles)
         int64_t tt = (int64_t)(std::sqrt(budget) / kTile + 0.5);
         tt = std::max<int64_t>(1, std::min<int64_t>(tt, P.tiles));
-        SymArgs sa;
+        SymArgs sa{};
         sa.pos = ra.pos; sa.N = std::min<int64_t>(P.N, tt * kTile); sa.tiles = tt;
-        sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2; sa.eps2 = ra.eps2;
+        sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2;
         int best = 0;
         double best_rate = 0.0;
         for (int v = 0; v < kSymVariants; ++v) {
@@ -535,7 +535,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
                             ctx->d_status, ctx->sms, st));
         ls.done(2);
     }
-    AttrArgs aa;
+    AttrArgs aa{};
     aa.tgt = pos; aa.N = P.N; aa.rho = rho; aa.coords = coords;
     aa.gxp = P.gxp; aa.ny = P.ny; aa.nz = P.nz;
     aa.rows_per_stage = kStageFloats / P.gxp;
@@ -543,7 +543,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     aa.x0 = g->lo + 0.5 * ((g->hi - g->lo) / P.nx);
     aa.part = at<dacc4>(ctx, P.o_parta); aa.status = ctx->d_status;
     aa.eps2 = eps2_of(ctx);
-    RepArgs ra;
+    RepArgs ra{};
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
     ra.eps2 = aa.eps2;
@@ -577,11 +577,11 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     if (ctx->rep_symmetric) {
         // every unordered pair once, exact fixed-point totals
         racc = at<unsigned long long>(ctx, P.o_racc);
-        SymArgs sa;
+        SymArgs sa{};
         sa.pos = pos; sa.N = P.N; sa.tiles = P.tiles;
         const int sv = ctx->sym_choice < 0 ? 0 : ctx->sym_choice;
         sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[energy ? 1 : 0][sv];
-        sa.acc = racc; sa.status = ctx->d_status;
+        sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2;
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
         CK(cudaMemsetAsync(racc, 0, (size_t)P.N * (energy ? 1 : 3) * sizeof(unsigned long long), st));
         CK(launch_repulsion_sym(sa, energy, sv, st));
@@ -591,7 +591,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         CK(launch_repulsion(ra, acc, energy, P.vr, st));
         ls.done();
     }
-    CombineArgs cb;
+    CombineArgs cb{};
     cb.N = P.N; cb.part_a = aa.part; cb.part_r = ra.part; cb.spa = P.spa; cb.spr = P.spr;
     cb.G = G; cb.A = A; cb.R = R;
     cb.G64 = g64 ? at<double>(ctx, P.o_g64) : nullptr;
@@ -673,7 +673,7 @@ int run_project(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns
                 const sparkling_proj *pr, const double *G64, double eta, const ProjPlan &L,
                 bool want_viol, cudaStream_t st)
 {
-    ProjArgs p;
+    ProjArgs p{};
     p.K = K; p.G = G64; p.eta = eta; p.Nc = Nc; p.Ns = (int)Ns;
     p.alpha = pr->alpha; p.beta = pr->beta; p.box = pr->box; p.tol = pr->tol;
     p.margin = pr->margin;
@@ -858,7 +858,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     sparkling_ctx::Batch &b = ctx->batch;
     CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0, (size_t)(b.B + 1) * sizeof(unsigned int),
                        st));
-    EngineArgs e;
+    EngineArgs e{};
     e.traj = at<EngineTraj>(ctx, b.o_traj);
     e.items = at<EngineItem>(ctx, b.o_items);
     e.n_items = (int32_t)n_items;

@@ -98,7 +98,7 @@ struct SymArgs {
     int64_t tiles;              // ceil(N / kTile)
     int64_t ctas;               // persistent CTAs; tri_count(tiles) units split evenly
     unsigned long long *acc;    // [N][NV] fixed-point sums (zeroed before the launch)
-    float eps2;                 // kernel sqrt(r^2 + eps^2): eps^2 (>= kEps2) added to every r^2
+    float eps2 = kEps2;         // kernel sqrt(r^2 + eps^2): eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -113,7 +113,7 @@ struct AttrArgs {
     float hx;             // grid spacing along x (columns are x0 + q hx)
     Split sp;             // per_tile = ny*nz rows
     dacc4 *part;        // [tiles][slots][kTile] (x, y, z, energy)
-    float eps2;           // eps^2 (>= kEps2) added to every r^2
+    float eps2 = kEps2;   // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -122,7 +122,7 @@ struct RepArgs {
     int64_t N;
     Split sp;             // per_tile = ceil(N / kSrcBlock) source blocks
     dacc4 *part;
-    float eps2;           // eps^2 (>= kEps2) added to every r^2
+    float eps2 = kEps2;   // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 
@@ -250,7 +250,7 @@ struct EngineArgs {
     unsigned int *queue;     // next item (reset to 0 before every launch)
     unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
     double *gstate;          // per-CTA projection state when it is not in shared memory
-    float eps2;              // eps^2 (>= kEps2) added to every r^2
+    float eps2 = kEps2;      // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
 

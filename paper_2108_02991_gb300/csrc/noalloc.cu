@@ -196,17 +196,17 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     NA_CK(launch_pack_positions(K, K_dtype, N, pos, status, sms, st));
     NA_CK(launch_pack_grid(grid->rho, nx, ny, nz, gxp, grid->lo, grid->hi, rho, coords, status, sms,
                            st));
-    AttrArgs aa;
+    AttrArgs aa{};
     aa.tgt = pos; aa.N = N; aa.rho = rho; aa.coords = coords;
     aa.gxp = gxp; aa.ny = ny; aa.nz = nz; aa.rows_per_stage = kStageFloats / gxp;
     aa.hx = (float)((grid->hi - grid->lo) / nx);
     aa.x0 = grid->lo + 0.5 * ((grid->hi - grid->lo) / nx);
     aa.sp = spa; aa.part = part_a; aa.status = status; aa.eps2 = kEps2;
     NA_CK(launch_attraction(aa, acc, false, kAttrDefault, st));
-    RepArgs ra;
+    RepArgs ra{};
     ra.pos = pos; ra.N = N; ra.sp = spr; ra.part = part_r; ra.status = status; ra.eps2 = kEps2;
     NA_CK(launch_repulsion(ra, acc, false, kRepDefault, st));
-    CombineArgs cb;
+    CombineArgs cb{};
     cb.N = N; cb.part_a = part_a; cb.part_r = part_r; cb.spa = spa; cb.spr = spr;
     cb.G = G; cb.A = nullptr; cb.R = nullptr; cb.G64 = nullptr;
     cb.scale = 1.0; cb.scale_dev = nullptr; cb.energy_blocks = nullptr; cb.racc = nullptr; cb.a_direct = nullptr;
