@@ -64,9 +64,14 @@ def test_grad_and_energy_regularised(sp, eps, acc):
         sp.sparkling_grad(ctx, Kd, g, acc, G=G, A=A, R=R)
         sp.sparkling_status(ctx)
         A0, R0, G0 = oracle.forces(K.astype(np.float64), grid, eps=eps)
-        assert_grad_close(G.cpu().numpy(), G0, f"G (eps {eps})")
         assert_grad_close(R.cpu().numpy(), R0, f"R (eps {eps})")
         assert_grad_close(A.cpu().numpy(), A0, f"A (eps {eps})")
+        # G = A - R: an eps far above the sample spacing (0.3) flattens both
+        # terms until they cancel to 1/40 of their size, and the subtraction's
+        # condition number (|A| + |R|) / (2 |G|) scales the relative gate there
+        cond = (np.linalg.norm(A0) + np.linalg.norm(R0)) / np.linalg.norm(G0) / 2
+        rel = 1e-5 if eps < 0.1 else 1e-5 * cond
+        assert_grad_close(G.cpu().numpy(), G0, f"G (eps {eps}, condition {cond:.1f})", rel=rel)
         F, Fa, Fr = sp.sparkling_energy(ctx, Kd, g, acc)
         F0, Fa0, Fr0 = oracle.energy(K.astype(np.float64), grid, eps=eps)
         assert Fa == pytest.approx(Fa0, rel=1e-6)
