@@ -19,6 +19,11 @@ NumPy arrays.  See the C file for the definitions followed:
 * ``violation`` -- the constraint checker;
 * ``step``    -- one projected-gradient step (eq. proj_grad_descent).
 
+Fast repulsion (particle-mesh split, see ``p3m.py`` for the mesh part):
+
+* ``repulsion_split`` -- exact short-range (erfc, cut at rc) and long-range
+  (erf) parts of the repulsion and of its distance sums.
+
 Algorithm 1 (multi-resolution SPARKLING):
 
 * ``upsample`` -- the linear interpolator L_{2d} between levels;
@@ -77,7 +82,9 @@ def _load():
                                             i64, i64, i64, d, d, d, d, p]
             lib.oracle_multires.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, i64, p,
                                             i64, i64, i64, i64, d, d, d, d, d, d, p, p]
-            for f in (lib.oracle_upsample, lib.oracle_optimize, lib.oracle_multires):
+            lib.oracle_repulsion_split.argtypes = [p, i64, d, d, d, p, i64, p, p, p, p]
+            for f in (lib.oracle_upsample, lib.oracle_optimize, lib.oracle_multires,
+                      lib.oracle_repulsion_split):
                 f.restype = ctypes.c_int
             for f in (lib.oracle_forces, lib.oracle_energy, lib.oracle_project,
                       lib.oracle_violation, lib.oracle_step):
@@ -251,3 +258,22 @@ def multires(K, Nc, Ns, grid, alpha, beta, box=0.5, pin_index=-1, pin=(0.0, 0.0,
         out.append(lev[o:o + n].copy())
         o += n
     return Kw, out, trace[:, :n_git]
+
+
+def repulsion_split(K, sigma, rc=0.0, eps=0.0, targets=None):
+    """(S, L, eS, eL): exact short-range (pairs closer than rc; rc <= 0: all)
+    and long-range parts of the repulsion sums and distance sums (not
+    scaled by 1/N) for the target indices (all if None)."""
+    K = _f64(K).reshape(-1, 3)
+    N = K.shape[0]
+    if targets is None:
+        tptr, M = None, N
+    else:
+        targets = np.ascontiguousarray(np.asarray(targets, dtype=np.int64))
+        tptr, M = _ptr(targets), targets.size
+    S = np.empty((M, 3)); L = np.empty((M, 3)); eS = np.empty(M); eL = np.empty(M)
+    st = _load().oracle_repulsion_split(_ptr(K), N, float(sigma), float(rc), float(eps), tptr, M,
+                                        _ptr(S), _ptr(L), _ptr(eS), _ptr(eL))
+    if st != OK:
+        raise ValueError(f"oracle_repulsion_split failed ({st})")
+    return S, L, eS, eL

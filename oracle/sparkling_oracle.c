@@ -559,3 +559,65 @@ int oracle_multires(double *K, int64_t Nc, int64_t Ns, const double *rho, int64_
     free(tmp);
     return st;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Split of the repulsion for a fast (particle-mesh) summation.             */
+
+/* The repulsion kernel d / |d|_eps = d / r (r = sqrt(|d|^2 + eps^2)) splits
+ * exactly into a short-range part d / r * erfc(r / sigma), which decays like
+ * a Gaussian, and a smooth long-range part d / r * erf(r / sigma) (the
+ * gradient of r erf(r/sigma) + sigma/sqrt(pi) exp(-r^2/sigma^2)).  For M
+ * targets (indices into K, or 0..N-1 when targets is NULL) this returns the
+ * directed sums over j != i of
+ *   S: the short-range part, only for pairs with |d| < rc (rc <= 0: all);
+ *   L: the long-range part (all pairs);
+ * and the matching energy sums eS (short: r erfc(r/sigma) -
+ * sigma/sqrt(pi) exp(-r^2/sigma^2), only |d| < rc) and eL (the long-range
+ * potential) -- none scaled by 1/N.  S + L (rc <= 0) is the repulsion sum
+ * and eS + eL the distance sum of oracle_forces.  Any output may be NULL. */
+int oracle_repulsion_split(const double *K, int64_t N, double sigma, double rc, double eps,
+                           const int64_t *targets, int64_t M, double *S, double *L, double *eS,
+                           double *eL)
+{
+    if (!K || N < 1 || !(sigma > 0) || M < 0 || !(eps >= 0.0))
+        return ORACLE_EINVAL;
+    const double spi = sigma / sqrt(3.14159265358979323846);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t m = 0; m < M; ++m) {
+        int64_t i = targets ? targets[m] : m;
+        if (i < 0 || i >= N) {
+            bad = 1;
+            continue;
+        }
+        double s[3] = {0, 0, 0}, l[3] = {0, 0, 0}, es = 0.0, el = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i)
+                continue;
+            double d[3] = {K[3 * i] - K[3 * j], K[3 * i + 1] - K[3 * j + 1],
+                           K[3 * i + 2] - K[3 * j + 2]};
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double r = sqrt(d2 + eps * eps);
+            if (r == 0.0)
+                continue;
+            double x = r / sigma;
+            double gauss = spi * exp(-x * x);
+            double wl = erf(x) / r, ws = erfc(x) / r;
+            for (int c = 0; c < 3; ++c)
+                l[c] += d[c] * wl;
+            el += r * erf(x) + gauss;
+            if (rc <= 0.0 || sqrt(d2) < rc) {
+                for (int c = 0; c < 3; ++c)
+                    s[c] += d[c] * ws;
+                es += r * erfc(x) - gauss;
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (S) S[3 * m + c] = s[c];
+            if (L) L[3 * m + c] = l[c];
+        }
+        if (eS) eS[m] = es;
+        if (eL) eL[m] = el;
+    }
+    return bad ? ORACLE_EINVAL : ORACLE_OK;
+}
