@@ -66,6 +66,7 @@ extern "C" {
 #define SPARKLING_E_TIMEOUT 5   /* a bounded device wait gave up (the kernel returned early) */
 #define SPARKLING_E_NOTCONV 6   /* converged-mode projection did not certify within n_iter */
 #define SPARKLING_E_IO 7        /* a checkpoint file could not be written */
+#define SPARKLING_E_RANGE 8     /* a sample lies outside the fast-repulsion mesh */
 
 /* Element types of K, G, A, R. */
 #define SPARKLING_F32 0
@@ -125,6 +126,22 @@ typedef struct sparkling_proj {
 /* How the attraction term is evaluated (sparkling_set_attraction). */
 #define SPARKLING_ATTRACTION_DIRECT 0   /* direct sum over the grid: O(N P) */
 #define SPARKLING_ATTRACTION_FIELD 1    /* interpolated node field: O(N), approximate */
+
+/* How the repulsion term is evaluated (sparkling_set_repulsion). */
+#define SPARKLING_REPULSION_DIRECT 0    /* every pair: O(N^2), exact */
+#define SPARKLING_REPULSION_MESH 1      /* particle-particle particle-mesh: ~O(N), approximate */
+
+/* Mesh of the fast repulsion.  The mesh covers [lo, hi]^3 with n_cells
+ * cells of side h = (hi - lo) / n_cells per axis plus g guard cells on each
+ * side (g >= 4, the smallest making n_cells + 2g a product of 2, 3, 5, 7);
+ * samples may lie up to g - 2 cells outside [lo, hi]. */
+typedef struct sparkling_mesh {
+    double lo, hi;         /* the samples' box */
+    double sigma_cells;    /* split width sigma in cells, > 0 (2.5: long-range error ~1e-6) */
+    double rc_sigmas;      /* short-range cut-off in units of sigma, >= 2 (4: erfc(4) = 1.5e-8) */
+    int32_t n_cells;       /* mesh cells across [lo, hi], 8 .. 1024 */
+    int32_t reserved;
+} sparkling_mesh;
 
 /* Flags of sparkling_step_batched. */
 #define SPARKLING_BATCH_GRAPH 1     /* replay the step from a cached CUDA graph */
@@ -334,6 +351,25 @@ SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps);
  *     outside [lo, hi] take the value of the nearest boundary cell.
  * Returns SPARKLING_E_INVAL for another mode. */
 SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
+
+/* Repulsion mode of the context's sparkling_grad, sparkling_energy,
+ * sparkling_energy_backward, sparkling_step, sparkling_step_host and driver
+ * calls (the batched step and sparkling_grad_noalloc always sum every pair).
+ *   SPARKLING_REPULSION_DIRECT (default; mesh may be NULL): every pair.
+ *   SPARKLING_REPULSION_MESH: the fast summation that replaces the paper's
+ *     fast multipole method (Sec. II-C.2), a particle-particle particle-mesh
+ *     split of the kernel d/|d|_eps = d/r erfc(r/sigma) + d/r erf(r/sigma):
+ *     the first part is summed directly over the pairs closer than
+ *     rc = rc_sigmas * sigma (a cell list), the second on the mesh (cubic
+ *     B-spline charges, FP32 FFT convolution with a deconvolved, tapered
+ *     kernel, interpolation back); the energy the same way with the matching
+ *     potential.  Approximate: its error against the direct sum is measured
+ *     by the caller.  The kernel spectra are built at the first call that
+ *     needs them (blocking, about 100 L^3 bytes of temporary device memory,
+ *     L = 4 (n_cells + 2g)), again when the mesh or the regularisation
+ *     changes.  A sample outside the mesh gives SPARKLING_E_RANGE.
+ * Returns SPARKLING_E_INVAL for a bad mode or mesh. */
+SPARKLING_API int sparkling_set_repulsion(sparkling_ctx *ctx, int mode, const sparkling_mesh *mesh);
 
 /* Build the node field of `grid`'s density for SPARKLING_ATTRACTION_FIELD
  * and keep it in the context (one field at a time, (n+2)^3 float4 on the

@@ -15,12 +15,13 @@ from typing import Optional, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsparkling.so")
 
-OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV, E_IO = range(8)
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV, E_IO, E_RANGE = range(9)
 F32, F64 = 0, 1
 ACC_KAHAN32, ACC_FP64 = 0, 1
 KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine", "driver")
 BATCH_GRAPH = 1
 ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
+REPULSION_DIRECT, REPULSION_MESH = 0, 1
 
 # Every entry point declared in include/sparkling.h.
 ABI_SYMBOLS = (
@@ -30,7 +31,7 @@ ABI_SYMBOLS = (
     "sparkling_launch_count", "sparkling_version", "sparkling_grad_noalloc",
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
     "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
-    "sparkling_upsample", "sparkling_optimize", "sparkling_multires",
+    "sparkling_upsample", "sparkling_optimize", "sparkling_multires", "sparkling_set_repulsion",
 )
 
 
@@ -53,6 +54,20 @@ class Proj(ctypes.Structure):
                 ("pin", ctypes.c_double * 3), ("pin_index", ctypes.c_int32),
                 ("n_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Mesh(ctypes.Structure):
+    """sparkling_mesh: the fast repulsion's mesh."""
+    _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double),
+                ("sigma_cells", ctypes.c_double), ("rc_sigmas", ctypes.c_double),
+                ("n_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def make_mesh(n_cells, sigma_cells=2.5, rc_sigmas=4.0, lo=-0.5, hi=0.5) -> Mesh:
+    m = Mesh()
+    m.lo, m.hi = float(lo), float(hi)
+    m.sigma_cells, m.rc_sigmas, m.n_cells = float(sigma_cells), float(rc_sigmas), int(n_cells)
+    return m
 
 
 class Schedule(ctypes.Structure):
@@ -107,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "sparkling_set_attraction": ([p, i], i),
             "sparkling_attraction_field": ([p, p, p], i),
             "sparkling_set_regularisation": ([p, ctypes.c_double], i),
+            "sparkling_set_repulsion": ([p, i, p], i),
             "sparkling_upsample": ([p, p, p, i, i64, i64, p], i),
             "sparkling_optimize": ([p, p, i, i64, i64, p, p, i, p, p, p], i),
             "sparkling_multires": ([p, p, i, i64, i64, p, p, i, p, ctypes.c_int32, ctypes.c_char_p,
@@ -368,6 +384,13 @@ def sparkling_set_attraction(ctx: Context, mode: int) -> None:
 def sparkling_set_regularisation(ctx: Context, eps: float) -> None:
     """Kernel H(r) = sqrt(r^2 + eps^2) for the context's later calls (0: |r|)."""
     _check(ctx, lib().sparkling_set_regularisation(ctx.handle, float(eps)))
+
+
+def sparkling_set_repulsion(ctx: Context, mode: int, mesh: Optional[Mesh] = None) -> None:
+    """REPULSION_DIRECT (every pair, default) or REPULSION_MESH (particle-
+    particle particle-mesh summation on `mesh`)."""
+    _check(ctx, lib().sparkling_set_repulsion(ctx.handle, int(mode),
+                                              ctypes.byref(mesh) if mesh is not None else None))
 
 
 def sparkling_attraction_field(ctx: Context, grid: Grid, stream=None) -> None:

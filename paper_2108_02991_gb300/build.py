@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparkling.so")
 SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "repulsion_sym.cu", "project.cu", "noalloc.cu",
-           "engine.cu", "field.cu", "driver.cu"]
+           "engine.cu", "field.cu", "driver.cu", "mesh.cu"]
 HEADERS = ["kernels.h", "ptx.cuh", "pair_dev.cuh", "project_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -90,6 +90,10 @@ struct sparkling_ctx {
     double field_lo = 0.0, field_hi = 0.0, field_eps = 0.0;
     // kernel H(r) = sqrt(r^2 + eps^2); eps = 0 is the plain norm
     double eps = 0.0;
+    // fast repulsion (mesh.cu)
+    int rep_mode = SPARKLING_REPULSION_DIRECT;
+    sparkling_mesh mesh_params = {};
+    MeshState *mesh = nullptr;
 };
 
 namespace {
@@ -284,7 +288,7 @@ struct PairPlan {
     int64_t tiles;
     int va, vr;            // tile shapes (autotuner variants) of the two pair kernels
     Split spa, spr;
-    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_racc, o_eblocks, o_g64, o_adir, end;
+    size_t o_pos, o_rho, o_coords, o_parta, o_partr, o_racc, o_eblocks, o_g64, o_adir, o_rdir, end;
 };
 
 int ensure_occupancy(sparkling_ctx *ctx)
@@ -364,6 +368,7 @@ int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, 
     P.o_eblocks = cv.take((size_t)energy_blocks(N) * sizeof(double2));
     P.o_g64 = need_g64 ? cv.take((size_t)N * 3 * sizeof(double)) : 0;
     P.o_adir = ctx->attr_mode == SPARKLING_ATTRACTION_FIELD ? cv.take((size_t)N * sizeof(dacc4)) : 0;
+    P.o_rdir = ctx->rep_mode == SPARKLING_REPULSION_MESH ? cv.take((size_t)N * sizeof(dacc4)) : 0;
     P.end = cv.off;
     return SPARKLING_OK;
 }
@@ -513,6 +518,40 @@ int build_field(sparkling_ctx *ctx, const sparkling_grid *g, cudaStream_t st)
     return SPARKLING_OK;
 }
 
+MeshConfig mesh_config(const sparkling_ctx *ctx)
+{
+    const sparkling_mesh &m = ctx->mesh_params;
+    MeshConfig c;
+    c.n_cells = m.n_cells;
+    c.lo = m.lo;
+    c.hi = m.hi;
+    c.sigma = m.sigma_cells * (m.hi - m.lo) / m.n_cells;
+    c.rc = m.rc_sigmas * c.sigma;
+    c.eps = ctx->eps;
+    return c;
+}
+
+// Kernel spectra of the context's mesh (built when the mesh or eps changed).
+int ensure_mesh(sparkling_ctx *ctx, cudaStream_t st)
+{
+    const MeshConfig c = mesh_config(ctx);
+    if (!ctx->mesh) ctx->mesh = mesh_state_create();
+    if (mesh_matches(ctx->mesh, c)) return SPARKLING_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(ctx, SPARKLING_E_INVAL, "the fast-repulsion mesh must be built outside stream capture");
+    const char *what = "";
+    cudaError_t e = mesh_build(ctx->mesh, c, ctx->sms, st, &what);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, SPARKLING_E_NOMEM, "fast repulsion: %s allocation failed", what);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    ctx->launches += 12;
+    return SPARKLING_OK;
+}
+
 // pack -> (autotune) -> attraction -> repulsion -> combine (gradient) or
 // energy reduction.  In field mode the attraction is the interpolated node
 // field.
@@ -547,9 +586,10 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     ra.pos = pos; ra.N = P.N; ra.part = at<dacc4>(ctx, P.o_partr);
     ra.status = ctx->d_status;
     ra.eps2 = aa.eps2;
+    const bool mesh_mode = ctx->rep_mode == SPARKLING_REPULSION_MESH;
     const bool need_a = !field_mode && attr_choice_of(ctx, acc, P.gxp) < 0,
-               need_r = !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
-               need_s = ctx->rep_symmetric && ctx->sym_choice < 0;
+               need_r = !mesh_mode && !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
+               need_s = !mesh_mode && ctx->rep_symmetric && ctx->sym_choice < 0;
     if (ctx->autotune && (need_a || need_r || need_s)) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(st, &cap));
@@ -574,7 +614,23 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         ls.done();
     }
     unsigned long long *racc = nullptr;
-    if (ctx->rep_symmetric) {
+    dacc4 *r_direct = nullptr;
+    if (mesh_mode) {
+        int s;
+        if ((s = ensure_mesh(ctx, st))) return s;
+        r_direct = at<dacc4>(ctx, P.o_rdir);
+        const char *what = "";
+        int nk = 0;
+        LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
+        cudaError_t e = mesh_eval(ctx->mesh, pos, P.N, energy, r_direct, ctx->d_status, ctx->sms, st,
+                                  &what, &nk);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(ctx, SPARKLING_E_NOMEM, "fast repulsion: %s allocation failed", what);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+        ls.done(nk);
+    } else if (ctx->rep_symmetric) {
         // every unordered pair once, exact fixed-point totals
         racc = at<unsigned long long>(ctx, P.o_racc);
         SymArgs sa{};
@@ -597,6 +653,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     cb.G64 = g64 ? at<double>(ctx, P.o_g64) : nullptr;
     cb.racc = racc;
     cb.a_direct = a_direct;
+    cb.r_direct = r_direct;
     cb.scale = scale;
     cb.scale_dev = scale_dev;
     cb.eps = ctx->eps;
@@ -624,6 +681,8 @@ int read_status(sparkling_ctx *ctx, cudaStream_t st)
         return fail(ctx, SPARKLING_E_TIMEOUT, "a bounded device wait ran out; results are incomplete");
     if (h & kDevNonFinite)
         return fail(ctx, SPARKLING_E_NONFINITE, "non-finite sample or density value, or negative density");
+    if (h & kDevRange)
+        return fail(ctx, SPARKLING_E_RANGE, "a sample lies outside the fast-repulsion mesh");
     return SPARKLING_OK;
 }
 
@@ -954,6 +1013,7 @@ SPARKLING_API void sparkling_destroy(sparkling_ctx *ctx)
         if (ctx->h_traj) cudaFreeHost(ctx->h_traj);
         cudaFree(ctx->ws);
         cudaFree(ctx->field);
+        mesh_state_destroy(ctx->mesh);
         cudaFree(ctx->h_K);
         cudaFree(ctx->h_rho);
         cudaFree(ctx->d_status);
@@ -1523,6 +1583,29 @@ SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps)
     if (!(eps >= 0.0) || !std::isfinite(eps) || eps > 1e3)
         return fail(ctx, SPARKLING_E_INVAL, "eps = %g must be finite, in [0, 1e3]", eps);
     ctx->eps = eps;
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_repulsion(sparkling_ctx *ctx, int mode, const sparkling_mesh *mesh)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (mode == SPARKLING_REPULSION_DIRECT) {
+        ctx->rep_mode = mode;
+        return SPARKLING_OK;
+    }
+    if (mode != SPARKLING_REPULSION_MESH)
+        return fail(ctx, SPARKLING_E_INVAL, "repulsion mode %d is not DIRECT/MESH", mode);
+    if (!mesh) return fail(ctx, SPARKLING_E_INVAL, "mesh is NULL");
+    if (!(std::isfinite(mesh->lo) && std::isfinite(mesh->hi) && mesh->hi > mesh->lo))
+        return fail(ctx, SPARKLING_E_INVAL, "mesh needs finite lo < hi");
+    if (mesh->n_cells < 8 || mesh->n_cells > 1024)
+        return fail(ctx, SPARKLING_E_INVAL, "mesh n_cells = %d must be in [8, 1024]", mesh->n_cells);
+    if (!(mesh->sigma_cells > 0) || !std::isfinite(mesh->sigma_cells) || mesh->sigma_cells > 64)
+        return fail(ctx, SPARKLING_E_INVAL, "mesh sigma_cells must be in (0, 64]");
+    if (!(mesh->rc_sigmas >= 2) || !std::isfinite(mesh->rc_sigmas) || mesh->rc_sigmas > 16)
+        return fail(ctx, SPARKLING_E_INVAL, "mesh rc_sigmas must be in [2, 16]");
+    ctx->rep_mode = mode;
+    ctx->mesh_params = *mesh;
     return SPARKLING_OK;
 }
 

@@ -18,6 +18,7 @@ constexpr float kEps2 = 1e-30f;        // smallest eps^2 added to every r^2 (zer
 // Device status bits (OR-ed into the context's status word).
 constexpr int kDevNonFinite = 1;
 constexpr int kDevTimeout = 2;
+constexpr int kDevRange = 4;            // a sample outside the fast-repulsion mesh
 
 // Four FP64 partial sums of one target: force (x, y, z) and energy (w).
 struct __align__(32) dacc4 {
@@ -135,6 +136,7 @@ struct CombineArgs {
     double *G64;          // optional FP64 copy of G [N][3]
     const unsigned long long *racc;   // symmetric repulsion sums [N][NV] (replaces part_r)
     const dacc4 *a_direct;            // attraction per target [N] (replaces part_a), or null
+    const dacc4 *r_direct;            // repulsion sums per target [N] (replaces racc/part_r), or null
     double scale;         // G, A, R are multiplied by scale * (*scale_dev if set)
     const double *scale_dev;
     double2 *energy_blocks;  // energy mode: per-block (sum ea, sum er)
@@ -180,6 +182,23 @@ cudaError_t field_build(const float *rho, int nx, int ny, int nz, double lo, dou
                         float4 *field, int sms, cudaStream_t st, const char **what);
 cudaError_t launch_interp(const float4 *pos, int64_t N, const float4 *field, int nx, int ny, int nz,
                           double lo, double hi, dacc4 *out, int sms, cudaStream_t st);
+
+// Fast repulsion (mesh.cu): particle-particle particle-mesh summation.
+struct MeshConfig {
+    int n_cells;          // mesh cells across [lo, hi]
+    double lo, hi;
+    double sigma, rc;     // split width and short-range cut-off (absolute units)
+    double eps;           // regularisation of the kernel
+};
+struct MeshState;
+MeshState *mesh_state_create();
+void mesh_state_destroy(MeshState *m);
+int mesh_guard(int n_cells);
+bool mesh_matches(const MeshState *m, const MeshConfig &c);
+cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t st,
+                       const char **what);
+cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, dacc4 *out,
+                      int *status, int sms, cudaStream_t st, const char **what, int *launches);
 
 // Multi-resolution driver (driver.cu).  dtype: 0 float, 1 double.
 cudaError_t launch_upsample(const void *Kc, void *Kf, int dtype, int64_t Nc, int64_t d, int sms,

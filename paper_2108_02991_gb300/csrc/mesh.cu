@@ -1,0 +1,600 @@
+// Fast repulsion: particle-particle particle-mesh (P3M) summation of
+// R_i = sum_{j != i} d_ij / |d_ij|_eps, the O(N^2) bottleneck of Sec. II-C.2
+// (the paper takes a fast multipole method there; this is the GB300 path).
+//
+// The kernel splits exactly: d/r = d/r erfc(r/sigma) + d/r erf(r/sigma),
+// r = |d|_eps.  The short-range part decays like a Gaussian and is summed
+// directly over the pairs closer than rc, found through a cell list (cells
+// of side >= rc, samples sorted by cell).  The long-range part is smooth and
+// is summed on a mesh:
+//   1. every sample spreads a unit charge to 4 x 4 x 4 nodes with cubic
+//      B-spline weights (64-bit fixed-point atomics: exact, order-free);
+//   2. the charge mesh (M^3 nodes, zero-padded to L = 2M per axis) is
+//      convolved with the long-range kernel by FP32 real FFTs (cuFFT);
+//   3. every sample gathers the four convolved fields (force x, y, z and the
+//      potential) from its 64 nodes with the same weights.
+// The kernel spectra are built once per mesh and eps: the kernel, tapered to
+// zero beyond every offset the mesh can have (a C-infinity step between
+// radius sqrt(3) M h and 2 M h), is sampled on a 4M box, transformed (FP64),
+// divided by the squared transform of the B-spline window (deconvolution),
+// transformed back, cut to the offsets |m| < M and transformed on the L box.
+// The taper keeps the deconvolution from amplifying a truncation edge (the
+// free-space convolution idea of Vico, Greengard and Ferrando, 2016).
+// The erfc of the short-range part is the rational approximation 7.1.26 of
+// Abramowitz and Stegun (|error| <= 1.5e-7) times exp(-x^2).
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.h"
+#include "ptx.cuh"
+
+namespace sparkling {
+
+namespace {
+
+constexpr int kMeshThreads = 256;
+constexpr double kFix = 4294967296.0;       // charge fixed point: round(w * 2^32)
+
+int grid_for(int64_t n, int sms)
+{
+    const int64_t b = (n + kMeshThreads - 1) / kMeshThreads, cap = (int64_t)sms * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// C-infinity step: 1 for t <= 0, 0 for t >= 1.
+__device__ double taper(double t)
+{
+    if (t <= 0.0) return 1.0;
+    if (t >= 1.0) return 0.0;
+    const double a = exp(-1.0 / (1.0 - t)), b = exp(-1.0 / t);
+    return a / (a + b);
+}
+
+// Component c (0..2 force, 3 potential) of the tapered long-range kernel
+// sampled at the offsets of the periodic 4M box (residue order).
+__global__ void fill_big_kernel(double *out, int Lb, double h, double sigma, double eps2,
+                                double r1, double r2, int c)
+{
+    const int64_t total = (int64_t)Lb * Lb * Lb;
+    const double spi = sigma * 0.56418958354775628;   // sigma / sqrt(pi)
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % Lb), iy = (int)((e / Lb) % Lb), iz = (int)(e / ((int64_t)Lb * Lb));
+        const double x = (ix <= Lb / 2 ? ix : ix - Lb) * h;
+        const double y = (iy <= Lb / 2 ? iy : iy - Lb) * h;
+        const double z = (iz <= Lb / 2 ? iz : iz - Lb) * h;
+        const double d2 = x * x + y * y + z * z;
+        const double r = sqrt(d2 + eps2), q = r / sigma;
+        const double chi = taper((sqrt(d2) - r1) / (r2 - r1));
+        double v;
+        if (c == 3) {
+            v = r * erf(q) + spi * exp(-q * q);
+        } else {
+            const double e_over_r = r > 0.0 ? erf(q) / r : 2.0 * 0.56418958354775628 / sigma;
+            v = (c == 0 ? x : (c == 1 ? y : z)) * e_over_r;
+        }
+        out[e] = v * chi;
+    }
+}
+
+// Division by the squared transform of the cubic B-spline window,
+// prod_a sinc(f_a)^8, f_a = frequency index / Lb in cycles per sample.
+__global__ void deconvolve_kernel(cufftDoubleComplex *k, int Lb)
+{
+    const int Lh = Lb / 2 + 1;
+    const int64_t total = (int64_t)Lb * Lb * Lh;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int fx = (int)(e % Lh), fy = (int)((e / Lh) % Lb), fz = (int)(e / ((int64_t)Lh * Lb));
+        const int f[3] = {fx, fy <= Lb / 2 ? fy : fy - Lb, fz <= Lb / 2 ? fz : fz - Lb};
+        double w = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            if (f[a] != 0) {
+                const double t = 3.14159265358979323846 * f[a] / Lb;
+                const double s = sin(t) / t;
+                const double s2 = s * s, s4 = s2 * s2;
+                w *= s4 * s4;
+            }
+        }
+        k[e].x /= w;
+        k[e].y /= w;
+    }
+}
+
+// The deconvolved kernel at the offsets |m_a| < M of the 4M box, placed in
+// the L = 2M box (residue order, offset M unused), scaled by `scale`.
+__global__ void extract_small_kernel(float *out, const double *big, int Lb, int L, int M,
+                                     double scale)
+{
+    const int64_t total = (int64_t)L * L * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % L), iy = (int)((e / L) % L), iz = (int)(e / ((int64_t)L * L));
+        if (ix == M || iy == M || iz == M) {
+            out[e] = 0.f;
+            continue;
+        }
+        const int mx = ix < M ? ix : ix - L, my = iy < M ? iy : iy - L, mz = iz < M ? iz : iz - L;
+        const int bx = (mx + Lb) % Lb, by = (my + Lb) % Lb, bz = (mz + Lb) % Lb;
+        out[e] = (float)(big[((int64_t)bz * Lb + by) * Lb + bx] * scale);
+    }
+}
+
+// Cubic B-spline weights of the 4 nodes first .. first + 3 around mesh
+// coordinate u (first = floor(u) - 1); u in double, weights in float.
+__device__ __forceinline__ void bspline_weights(double u, int &first, float w[4])
+{
+    const double fl = floor(u);
+    first = (int)fl - 1;
+    const float f = (float)(u - fl), g = 1.f - f, f2 = f * f, f3 = f2 * f;
+    w[0] = g * g * g * (1.f / 6.f);
+    w[1] = (3.f * f3 - 6.f * f2 + 4.f) * (1.f / 6.f);
+    w[2] = (-3.f * f3 + 3.f * f2 + 3.f * f + 1.f) * (1.f / 6.f);
+    w[3] = f3 * (1.f / 6.f);
+}
+
+struct NodeWeights {
+    int first[3];
+    float w[3][4];
+    bool ok;
+};
+
+__device__ __forceinline__ NodeWeights node_weights(float4 p, double x0, double inv_h, int M)
+{
+    NodeWeights nw;
+    const double u[3] = {((double)p.x - x0) * inv_h, ((double)p.y - x0) * inv_h,
+                         ((double)p.z - x0) * inv_h};
+    nw.ok = true;
+    for (int a = 0; a < 3; ++a) {
+        const bool in = u[a] >= 1.0 && u[a] < (double)(M - 2);
+        nw.ok = nw.ok && in;
+        bspline_weights(in ? u[a] : 1.0, nw.first[a], nw.w[a]);
+    }
+    return nw;
+}
+
+// Unit charges of the samples on the M^3 charge mesh (fixed point).
+__global__ void spread_kernel(const float4 *__restrict__ pos, int64_t N, unsigned long long *Q,
+                              double x0, double inv_h, int M, int *status)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const NodeWeights nw = node_weights(pos[i], x0, inv_h, M);
+        if (!nw.ok) {
+            bad = 1;
+            continue;
+        }
+        for (int c = 0; c < 4; ++c)
+            for (int b = 0; b < 4; ++b) {
+                const float wzy = nw.w[2][c] * nw.w[1][b];
+                unsigned long long *row =
+                    Q + ((int64_t)(nw.first[2] + c) * M + (nw.first[1] + b)) * M + nw.first[0];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const long long v = __double2ll_rn((double)(wzy * nw.w[0][a]) * kFix);
+                    if (v) atomicAdd(row + a, (unsigned long long)v);
+                }
+            }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kDevRange);
+}
+
+// Fixed-point charges -> the zero-padded real L^3 box.
+__global__ void charges_to_box_kernel(const unsigned long long *__restrict__ Q, float *box, int M,
+                                      int L)
+{
+    const int64_t total = (int64_t)L * L * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % L), iy = (int)((e / L) % L), iz = (int)(e / ((int64_t)L * L));
+        float v = 0.f;
+        if (ix < M && iy < M && iz < M)
+            v = (float)((double)(long long)Q[((int64_t)iz * M + iy) * M + ix] * (1.0 / kFix));
+        box[e] = v;
+    }
+}
+
+// out = a * b (complex), n elements.
+__global__ void spectrum_product_kernel(cufftComplex *out, const cufftComplex *__restrict__ a,
+                                        const cufftComplex *__restrict__ b, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const cufftComplex x = a[e], y = b[e];
+        out[e] = make_cuFloatComplex(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+    }
+}
+
+// Long-range sums gathered from the four convolved fields (L^3 boxes; node n
+// of the mesh is box index n), plus the short-range sums: out = S + L.
+__global__ void gather_kernel(const float4 *__restrict__ pos, int64_t N,
+                              const float *__restrict__ phi, int64_t box, int L, double x0,
+                              double inv_h, int M, int ncomp, const dacc4 *__restrict__ shortr,
+                              dacc4 *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const NodeWeights nw = node_weights(pos[i], x0, inv_h, M);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (nw.ok) {
+            for (int c = 0; c < 4; ++c)
+                for (int b = 0; b < 4; ++b) {
+                    const float wzy = nw.w[2][c] * nw.w[1][b];
+                    const int64_t row = ((int64_t)(nw.first[2] + c) * L + (nw.first[1] + b)) * L +
+                                        nw.first[0];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float w = wzy * nw.w[0][a];
+                        for (int k = 0; k < ncomp; ++k)
+                            acc[k] = fmaf(w, __ldg(phi + k * box + row + a), acc[k]);
+                    }
+                }
+        }
+        const dacc4 s = shortr[i];
+        dacc4 r;
+        r.x = s.x + (double)acc[0];
+        r.y = s.y + (double)acc[1];
+        r.z = s.z + (double)acc[2];
+        r.w = s.w + (double)acc[3];
+        out[i] = r;
+    }
+}
+
+// ---- short-range part ------------------------------------------------------
+
+__device__ __forceinline__ int cell_coord(float x, float x0, float inv_cs, int nc)
+{
+    int c = (int)floorf((x - x0) * inv_cs);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void cell_keys_kernel(const float4 *__restrict__ pos, int64_t N, float x0, float inv_cs,
+                                 int nc, unsigned int *keys, int *vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        const int cx = cell_coord(p.x, x0, inv_cs, nc), cy = cell_coord(p.y, x0, inv_cs, nc),
+                  cz = cell_coord(p.z, x0, inv_cs, nc);
+        keys[i] = (unsigned int)((cz * nc + cy) * nc + cx);
+        vals[i] = (int)i;
+    }
+}
+
+// Cell ranges [start, end) of the sorted keys (cells without samples keep
+// start = end = 0) and the samples' positions in sorted order.
+__global__ void cell_ranges_kernel(const unsigned int *__restrict__ keys,
+                                   const int *__restrict__ idx, const float4 *__restrict__ pos,
+                                   int64_t N, int *start, int *end, float4 *spos)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned int c = keys[k];
+        if (k == 0 || keys[k - 1] != c) start[c] = (int)k;
+        if (k == N - 1 || keys[k + 1] != c) end[c] = (int)(k + 1);
+        spos[k] = pos[idx[k]];
+    }
+}
+
+// erfc(x), x >= 0: Abramowitz & Stegun 7.1.26 polynomial in t = 1/(1 + p x)
+// times exp(-x^2) (returned separately, the energy needs it too).
+__device__ __forceinline__ float erfc_as(float x, float &gauss)
+{
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    gauss = __expf(-x * x);
+    return t * poly * gauss;
+}
+
+// One thread per sample in cell order: the short-range sums over the 27
+// cells around the sample's cell, pairs with |d| < rc.  The self pair adds
+// nothing to the force and g_short(0) to the potential.
+template <bool ENERGY>
+__global__ void __launch_bounds__(kMeshThreads) short_kernel(
+    const float4 *__restrict__ spos, const int *__restrict__ idx, const int *__restrict__ start,
+    const int *__restrict__ end, int64_t N, int nc, float x0, float inv_cs, float rc2,
+    float inv_sigma, float spi, float eps2, dacc4 *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = spos[k];
+        const int cx = cell_coord(p.x, x0, inv_cs, nc), cy = cell_coord(p.y, x0, inv_cs, nc),
+                  cz = cell_coord(p.z, x0, inv_cs, nc);
+        double sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= nc) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= nc) continue;
+                // the three x-neighbours are consecutive cells: one range
+                const int xa = cx > 0 ? cx - 1 : 0, xb = cx < nc - 1 ? cx + 1 : nc - 1;
+                const int base = (z * nc + y) * nc;
+                int j0 = -1, j1 = -1;
+                for (int x = xa; x <= xb; ++x) {
+                    const int s = start[base + x], e = end[base + x];
+                    if (s < e) {
+                        if (j0 < 0) j0 = s;
+                        j1 = e;
+                    }
+                }
+                if (j0 < 0) continue;
+                float fx = 0.f, fy = 0.f, fz = 0.f, fe = 0.f;
+                for (int j = j0; j < j1; ++j) {
+                    const float4 q = spos[j];
+                    const float ddx = p.x - q.x, ddy = p.y - q.y, ddz = p.z - q.z;
+                    const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                    if (d2 < rc2) {
+                        const float re2 = d2 + eps2;
+                        const float ri = rsqrt_sfu(fmaxf(re2, kEps2));
+                        const float r = re2 * ri;
+                        float gauss;
+                        const float ec = erfc_as(r * inv_sigma, gauss);
+                        const float w = ec * ri;
+                        fx = fmaf(ddx, w, fx);
+                        fy = fmaf(ddy, w, fy);
+                        fz = fmaf(ddz, w, fz);
+                        if (ENERGY) fe += fmaf(r, ec, -spi * gauss);
+                    }
+                }
+                sx += fx; sy += fy; sz += fz; se += fe;
+            }
+        }
+        out[idx[k]] = make_dacc4(sx, sy, sz, se);
+    }
+}
+
+} // namespace
+
+// ---- host side ---------------------------------------------------------------
+
+namespace {
+
+bool seven_smooth(int n)
+{
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+template <typename T> cudaError_t grow(T *&p, size_t &cap, size_t bytes)
+{
+    if (bytes <= cap) return cudaSuccess;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+}
+
+} // namespace
+
+struct MeshState {
+    MeshConfig cfg;          // the mesh the spectra were built for
+    bool built = false;
+    int M = 0, L = 0, nc = 0;
+    double x0 = 0.0;
+    cufftComplex *spectra = nullptr;   // 4 kernel spectra on the L box (scaled by 1/L^3)
+    size_t spectra_cap = 0;
+    cufftHandle r2c = 0, c2r = 0;
+    bool plans = false;
+    // evaluation buffers (grow with N)
+    unsigned long long *Q = nullptr; size_t Q_cap = 0;
+    float *box = nullptr; size_t box_cap = 0;           // charges, then 4 fields
+    cufftComplex *qhat = nullptr; size_t qhat_cap = 0;
+    cufftComplex *tmp = nullptr; size_t tmp_cap = 0;
+    unsigned int *keys = nullptr; size_t keys_cap = 0;   // 2N keys, 2N values
+    int *vals = nullptr; size_t vals_cap = 0;
+    int *ranges = nullptr; size_t ranges_cap = 0;        // start[nc^3], end[nc^3]
+    float4 *spos = nullptr; size_t spos_cap = 0;
+    dacc4 *shortr = nullptr; size_t shortr_cap = 0;
+    void *cub = nullptr; size_t cub_cap = 0;
+};
+
+MeshState *mesh_state_create() { return new MeshState(); }
+
+void mesh_state_destroy(MeshState *m)
+{
+    if (!m) return;
+    if (m->plans) { cufftDestroy(m->r2c); cufftDestroy(m->c2r); }
+    cudaFree(m->spectra); cudaFree(m->Q); cudaFree(m->box); cudaFree(m->qhat); cudaFree(m->tmp);
+    cudaFree(m->keys); cudaFree(m->vals); cudaFree(m->ranges); cudaFree(m->spos);
+    cudaFree(m->shortr); cudaFree(m->cub);
+    delete m;
+}
+
+int mesh_guard(int n_cells)
+{
+    int g = 4;
+    while (!seven_smooth(n_cells + 2 * g)) ++g;
+    return g;
+}
+
+bool mesh_matches(const MeshState *m, const MeshConfig &c)
+{
+    return m->built && m->cfg.n_cells == c.n_cells && m->cfg.lo == c.lo && m->cfg.hi == c.hi &&
+           m->cfg.sigma == c.sigma && m->cfg.rc == c.rc && m->cfg.eps == c.eps;
+}
+
+// Kernel spectra and FFT plans of mesh c (blocking; allocates the 4M box for
+// the duration of the call).
+cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t st,
+                       const char **what)
+{
+    m->built = false;
+    const int g = mesh_guard(c.n_cells);
+    const int M = c.n_cells + 2 * g, L = 2 * M, Lb = 4 * M;
+    const double h = (c.hi - c.lo) / c.n_cells;
+    const int64_t nb = (int64_t)Lb * Lb * Lb, nbc = (int64_t)Lb * Lb * (Lb / 2 + 1);
+    const int64_t nl = (int64_t)L * L * L, nlc = (int64_t)L * L * (L / 2 + 1);
+    double *big = nullptr;
+    cufftDoubleComplex *bigc = nullptr;
+    float *small = nullptr;
+    void *work = nullptr;
+    cufftHandle fwd = 0, inv = 0, sfwd = 0;
+    bool hf = false, hi = false, hs = false;
+    cudaError_t err = cudaSuccess;
+    auto done = [&](cudaError_t e) {
+        if (hf) cufftDestroy(fwd);
+        if (hi) cufftDestroy(inv);
+        if (hs) cufftDestroy(sfwd);
+        cudaFree(big);
+        cudaFree(bigc);
+        cudaFree(small);
+        cudaFree(work);
+        return e;
+    };
+    // the three plans run one after another: one shared work area
+    auto plan = [](cufftHandle *p, int n, cufftType t, size_t *ws, bool &made) {
+        if (cufftCreate(p) != CUFFT_SUCCESS) return false;
+        made = true;
+        return cufftSetAutoAllocation(*p, 0) == CUFFT_SUCCESS &&
+               cufftMakePlan3d(*p, n, n, n, t, ws) == CUFFT_SUCCESS;
+    };
+    *what = "mesh kernel buffers";
+    if ((err = grow(m->spectra, m->spectra_cap, (size_t)4 * nlc * sizeof(cufftComplex))) != cudaSuccess)
+        return done(err);
+    if ((err = cudaMalloc(&big, nb * sizeof(double))) != cudaSuccess) return done(err);
+    if ((err = cudaMalloc(&bigc, nbc * sizeof(cufftDoubleComplex))) != cudaSuccess) return done(err);
+    if ((err = cudaMalloc(&small, nl * sizeof(float))) != cudaSuccess) return done(err);
+    *what = "mesh cuFFT plans";
+    size_t w1 = 0, w2 = 0, w3 = 0;
+    if (!plan(&fwd, Lb, CUFFT_D2Z, &w1, hf) || !plan(&inv, Lb, CUFFT_Z2D, &w2, hi) ||
+        !plan(&sfwd, L, CUFFT_R2C, &w3, hs))
+        return done(cudaErrorUnknown);
+    *what = "mesh cuFFT work area";
+    if ((err = cudaMalloc(&work, std::max(std::max(w1, w2), std::max(w3, (size_t)256)))) != cudaSuccess)
+        return done(err);
+    if (cufftSetWorkArea(fwd, work) != CUFFT_SUCCESS || cufftSetWorkArea(inv, work) != CUFFT_SUCCESS ||
+        cufftSetWorkArea(sfwd, work) != CUFFT_SUCCESS || cufftSetStream(fwd, st) != CUFFT_SUCCESS ||
+        cufftSetStream(inv, st) != CUFFT_SUCCESS || cufftSetStream(sfwd, st) != CUFFT_SUCCESS)
+        return done(cudaErrorUnknown);
+    *what = "mesh kernel spectra";
+    const double r1 = std::sqrt(3.0) * M * h, r2 = 2.0 * M * h;
+    const double scale = 1.0 / ((double)nb * (double)nl);
+    for (int comp = 0; comp < 4; ++comp) {
+        fill_big_kernel<<<grid_for(nb, sms), kMeshThreads, 0, st>>>(big, Lb, h, c.sigma,
+                                                                   c.eps * c.eps, r1, r2, comp);
+        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
+        if (cufftExecD2Z(fwd, big, bigc) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+        deconvolve_kernel<<<grid_for(nbc, sms), kMeshThreads, 0, st>>>(bigc, Lb);
+        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
+        if (cufftExecZ2D(inv, bigc, big) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+        extract_small_kernel<<<grid_for(nl, sms), kMeshThreads, 0, st>>>(small, big, Lb, L, M,
+                                                                        scale);
+        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
+        if (cufftExecR2C(sfwd, small, m->spectra + comp * nlc) != CUFFT_SUCCESS)
+            return done(cudaErrorUnknown);
+    }
+    if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return done(err);
+    // evaluation plans on the L box
+    *what = "mesh evaluation plans";
+    if (m->plans) {
+        cufftDestroy(m->r2c);
+        cufftDestroy(m->c2r);
+        m->plans = false;
+    }
+    if (cufftPlan3d(&m->r2c, L, L, L, CUFFT_R2C) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+    if (cufftPlan3d(&m->c2r, L, L, L, CUFFT_C2R) != CUFFT_SUCCESS) {
+        cufftDestroy(m->r2c);
+        return done(cudaErrorUnknown);
+    }
+    m->plans = true;
+    m->cfg = c;
+    m->M = M;
+    m->L = L;
+    m->x0 = c.lo - g * h;
+    const double span = M * h;
+    m->nc = (int)std::floor(span / c.rc);
+    if (m->nc < 1) m->nc = 1;
+    if (m->nc > 256) m->nc = 256;
+    m->built = true;
+    *what = "";
+    return done(cudaSuccess);
+}
+
+// Repulsion sums of the N packed samples into out[i] = (sum d/r, sum |d|_eps)
+// over all j (directed, the self pair included as eps in the potential).
+cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, dacc4 *out,
+                      int *status, int sms, cudaStream_t st, const char **what, int *launches)
+{
+    const MeshConfig &c = m->cfg;
+    const int M = m->M, L = m->L, nc = m->nc;
+    const int64_t nm = (int64_t)M * M * M, nl = (int64_t)L * L * L, nlc = (int64_t)L * L * (L / 2 + 1);
+    const int ncomp = energy ? 4 : 3;
+    const int64_t ncell = (int64_t)nc * nc * nc;
+    const double h = (c.hi - c.lo) / c.n_cells;
+    cudaError_t err;
+    *what = "mesh evaluation buffers";
+    size_t cub_bytes = 0;
+    int end_bit = 1;
+    while (((int64_t)1 << end_bit) < ncell) ++end_bit;
+    cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, m->keys, m->keys, m->vals, m->vals,
+                                    (int)N, 0, end_bit, st);
+    if ((err = grow(m->Q, m->Q_cap, nm * sizeof(unsigned long long))) ||
+        (err = grow(m->box, m->box_cap, (size_t)(ncomp + 1) * nl * sizeof(float))) ||
+        (err = grow(m->qhat, m->qhat_cap, nlc * sizeof(cufftComplex))) ||
+        (err = grow(m->tmp, m->tmp_cap, nlc * sizeof(cufftComplex))) ||
+        (err = grow(m->keys, m->keys_cap, (size_t)2 * N * sizeof(unsigned int))) ||
+        (err = grow(m->vals, m->vals_cap, (size_t)2 * N * sizeof(int))) ||
+        (err = grow(m->ranges, m->ranges_cap, (size_t)2 * ncell * sizeof(int))) ||
+        (err = grow(m->spos, m->spos_cap, (size_t)N * sizeof(float4))) ||
+        (err = grow(m->shortr, m->shortr_cap, (size_t)N * sizeof(dacc4))) ||
+        (err = grow(m->cub, m->cub_cap, cub_bytes + 256)))
+        return err;
+    if (cufftSetStream(m->r2c, st) != CUFFT_SUCCESS || cufftSetStream(m->c2r, st) != CUFFT_SUCCESS)
+        return cudaErrorUnknown;
+    *what = "mesh evaluation";
+    const int gN = grid_for(N, sms);
+    // short-range part: cell list sorted by cell, then the pair sums
+    const float cs = (float)(M * h / nc);
+    cell_keys_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, (float)m->x0, 1.f / cs, nc, m->keys,
+                                                  m->vals);
+    if ((err = cub::DeviceRadixSort::SortPairs(m->cub, cub_bytes, m->keys, m->keys + N, m->vals,
+                                               m->vals + N, (int)N, 0, end_bit, st)))
+        return err;
+    if ((err = cudaMemsetAsync(m->ranges, 0, (size_t)2 * ncell * sizeof(int), st))) return err;
+    cell_ranges_kernel<<<gN, kMeshThreads, 0, st>>>(m->keys + N, m->vals + N, pos, N, m->ranges,
+                                                    m->ranges + ncell, m->spos);
+    const float rc2 = (float)(c.rc * c.rc), inv_sigma = (float)(1.0 / c.sigma);
+    const float spi = (float)(c.sigma * 0.56418958354775628);
+    const float eps2 = (float)(c.eps * c.eps);
+    if (energy)
+        short_kernel<true><<<gN, kMeshThreads, 0, st>>>(m->spos, m->vals + N, m->ranges,
+                                                        m->ranges + ncell, N, nc, (float)m->x0,
+                                                        1.f / cs, rc2, inv_sigma, spi, eps2,
+                                                        m->shortr);
+    else
+        short_kernel<false><<<gN, kMeshThreads, 0, st>>>(m->spos, m->vals + N, m->ranges,
+                                                         m->ranges + ncell, N, nc, (float)m->x0,
+                                                         1.f / cs, rc2, inv_sigma, spi, eps2,
+                                                         m->shortr);
+    // long-range part
+    if ((err = cudaMemsetAsync(m->Q, 0, nm * sizeof(unsigned long long), st))) return err;
+    spread_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, m->Q, m->x0, 1.0 / h, M, status);
+    charges_to_box_kernel<<<grid_for(nl, sms), kMeshThreads, 0, st>>>(m->Q, m->box, M, L);
+    if (cufftExecR2C(m->r2c, m->box, m->qhat) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    for (int k = 0; k < ncomp; ++k) {
+        spectrum_product_kernel<<<grid_for(nlc, sms), kMeshThreads, 0, st>>>(
+            m->tmp, m->qhat, m->spectra + k * nlc, nlc);
+        if (cufftExecC2R(m->c2r, m->tmp, m->box + (1 + k) * nl) != CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+    }
+    gather_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, m->box + nl, nl, L, m->x0, 1.0 / h, M, ncomp,
+                                               m->shortr, out);
+    *launches = 8 + 2 * ncomp;
+    *what = "";
+    return cudaGetLastError();
+}
+
+} // namespace sparkling

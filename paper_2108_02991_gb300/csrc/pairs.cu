@@ -125,7 +125,9 @@ __global__ void combine_kernel(const CombineArgs c)
          i += (int64_t)gridDim.x * blockDim.x) {
         dacc4 a = c.a_direct ? c.a_direct[i] : sum_slots(c.part_a, c.spa, i);
         dacc4 r;
-        if (c.racc) {
+        if (c.r_direct) {
+            r = c.r_direct[i];
+        } else if (c.racc) {
             r.x = (double)(long long)c.racc[3 * i] / kFixScale;
             r.y = (double)(long long)c.racc[3 * i + 1] / kFixScale;
             r.z = (double)(long long)c.racc[3 * i + 2] / kFixScale;
@@ -179,7 +181,9 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_block_kernel(const Comb
         const int64_t i = (int64_t)blockIdx.x * kEnergyBlock + k * kEnergyThreads + threadIdx.x;
         if (i < c.N) {
             ea += c.a_direct ? c.a_direct[i].w : sum_slots(c.part_a, c.spa, i).w;
-            er += c.racc ? (double)(long long)c.racc[i] / kFixScale : sum_slots(c.part_r, c.spr, i).w;
+            er += c.r_direct ? c.r_direct[i].w
+                             : c.racc ? (double)(long long)c.racc[i] / kFixScale
+                                      : sum_slots(c.part_r, c.spr, i).w;
         }
     }
     const double2 s = block_sum2(ea, er);

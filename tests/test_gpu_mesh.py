@@ -1,0 +1,161 @@
+"""Fast repulsion (SPARKLING_REPULSION_MESH): the particle-particle
+particle-mesh summation through the C ABI.
+
+* parity: the library's R equals the oracle's P3M result -- the exact
+  short-range sum cut at rc plus the NumPy particle-mesh long-range sum
+  (``oracle/p3m.py``) -- to float rounding;
+* method error: against the exact direct repulsion (oracle) it is measured
+  and must stay within the bound stated in each test;
+* a sample outside the mesh is reported, repeated calls are bitwise equal.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from gpu_util import assert_grad_close, rel_l2
+from oracle import p3m
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_02991_gb300 import build
+    build.build()
+    import paper_2108_02991_gb300 as m
+    return m
+
+
+def guard(n_cells):
+    """Guard cells the library adds: the smallest g >= 4 with n_cells + 2g
+    a product of 2, 3, 5 and 7."""
+    g = 4
+    while True:
+        m = n_cells + 2 * g
+        for p in (2, 3, 5, 7):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return g
+        g += 1
+
+
+def mesh_ctx(sp, n_cells, sigma_cells=2.5, rc_sigmas=4.0, eps=0.0):
+    c = sp.sparkling_create(0)
+    sp.sparkling_set_repulsion(c, sp.REPULSION_MESH, sp.make_mesh(n_cells, sigma_cells, rc_sigmas))
+    if eps:
+        sp.sparkling_set_regularisation(c, eps)
+    return c
+
+
+def gpu_grad(sp, ctx, K, grid):
+    Kd = torch.from_numpy(np.ascontiguousarray(K, np.float32)).cuda()
+    rho = torch.from_numpy(grid.rho).cuda()
+    g = sp.make_grid(rho, grid.lo, grid.hi, grid.n)
+    G = torch.empty(K.shape[0], 3, dtype=torch.float64, device="cuda")
+    R = torch.empty_like(G)
+    sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G, R=R)
+    sp.sparkling_status(ctx)
+    F = sp.sparkling_energy(ctx, Kd, g, sp.ACC_KAHAN32)
+    return G.cpu().numpy(), R.cpu().numpy(), F
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_mesh_matches_p3m_oracle_and_direct_sum(sp, eps):
+    """3000 samples (a coincident pair and one sample 1.5 cells outside the
+    box included), 24 mesh cells, sigma = 2.5 cells, rc = 4 sigma."""
+    n_cells, sc, rs = 24, 2.5, 4.0
+    rng = np.random.default_rng(61)
+    K = rng.uniform(-0.5, 0.5, size=(3000, 3)).astype(np.float32)
+    K[1] = K[0]
+    K[7] = [0.5 + 1.5 / n_cells, 0.1, -0.2]
+    K64 = K.astype(np.float64)
+    N = K.shape[0]
+    grid = inputs.density_gaussian(8, 0.2)
+    ctx = mesh_ctx(sp, n_cells, sc, rs, eps)
+    try:
+        G, R, (F, Fa, Fr) = gpu_grad(sp, ctx, K, grid)
+    finally:
+        ctx.close()
+    spec = p3m.MeshSpec(n_cells=n_cells, sigma=sc / n_cells, guard=guard(n_cells))
+    S, _, eS, _ = oracle.repulsion_split(K64, spec.sigma, rc=rs * spec.sigma, eps=eps)
+    Lm, eLm = p3m.mesh_long(K64, spec, eps)
+    want = (S + Lm) / N
+    # parity with the P3M oracle: float sums of ~N unit vectors, FP32 FFTs
+    assert_grad_close(R, want, "R (mesh) vs the P3M oracle", rel=3e-6, atol=2e-6)
+    # method error against the exact direct sum
+    A0, R0, G0 = oracle.forces(K64, grid, eps=eps)
+    e = rel_l2(R, R0)
+    print(f"mesh repulsion 24 cells, eps {eps}: R rel L2 {e:.2e} against the direct sum")
+    assert e < 1e-5
+    assert_grad_close(G, G0, "G (mesh repulsion)", rel=1e-4, atol=1e-5)
+    # energy: the library's directed distance sums include the self pair of
+    # every sample on both sides -- the short-range sum adds
+    # g_short(eps) = eps erfc(eps/sigma) - sigma/sqrt(pi) exp(-eps^2/sigma^2),
+    # the mesh potential its own approximation of g_long(eps) (as the NumPy
+    # mesh does), together eps -- and the reduction removes N eps
+    x = eps / spec.sigma
+    g_short0 = eps * math.erfc(x) - spec.sigma / math.sqrt(math.pi) * math.exp(-x * x)
+    er_p3m = eS.sum() + N * g_short0 + eLm.sum()
+    Fr_p3m = (er_p3m - N * eps) / (2.0 * N * N)
+    _, _, Fr0 = oracle.energy(K64, grid, eps=eps)
+    assert Fr == pytest.approx(Fr_p3m, rel=2e-6)
+    assert Fr == pytest.approx(Fr0, rel=2e-5)
+
+
+def test_mesh_repeatable_and_range_error(sp):
+    n_cells = 32
+    rng = np.random.default_rng(62)
+    K = rng.uniform(-0.45, 0.45, size=(5000, 3)).astype(np.float32)
+    grid = inputs.density_gaussian(8, 0.2)
+    ctx = mesh_ctx(sp, n_cells)
+    try:
+        G1, R1, F1 = gpu_grad(sp, ctx, K, grid)
+        G2, R2, F2 = gpu_grad(sp, ctx, K, grid)
+        np.testing.assert_array_equal(R1, R2)
+        assert F1 == F2
+        Kb = K.copy()
+        Kb[3] = [0.5 + 3.5 / n_cells, 0.0, 0.0]      # beyond the guard cells
+        with pytest.raises(sp.SparklingError) as e:
+            gpu_grad(sp, ctx, Kb, grid)
+        assert e.value.code == sp.E_RANGE
+        G3, _, _ = gpu_grad(sp, ctx, K, grid)          # the context stays usable
+        np.testing.assert_array_equal(G3, G1)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("name,n_cells,m", [("diff", 128, 128), ("hr", 256, 64)])
+def test_mesh_full_size_sampled_targets(sp, name, n_cells, m):
+    """Full-size workloads with the mesh repulsion (sigma = 2.5 cells, rc = 4
+    sigma): R and G on sampled targets against the oracle's direct sums."""
+    p = inputs.make_problem(name)
+    ctx = mesh_ctx(sp, n_cells)
+    try:
+        Kd = torch.from_numpy(p.K).cuda()
+        rho = torch.from_numpy(p.grid.rho).cuda()
+        g = sp.make_grid(rho, p.grid.lo, p.grid.hi, p.grid.n)
+        G = torch.empty(p.N, 3, dtype=torch.float64, device="cuda")
+        R = torch.empty_like(G)
+        sp.sparkling_set_timing(ctx, True)
+        sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G, R=R)
+        sp.sparkling_status(ctx)
+        t = sp.sparkling_kernel_times(ctx)
+    finally:
+        ctx.close()
+    idx = np.sort(np.random.default_rng(63).choice(p.N, size=m, replace=False))
+    _, R0, G0 = oracle.forces(p.K.astype(np.float64), p.grid, targets=idx)
+    eR = rel_l2(R.cpu().numpy()[idx], R0)
+    eG = rel_l2(G.cpu().numpy()[idx], G0)
+    print(f"mesh repulsion {name} ({n_cells} cells): R rel L2 {eR:.2e}, G rel L2 {eG:.2e}, "
+          f"repulsion {t['repulsion'][0]:.1f} ms (first call, with the kernel spectra)")
+    assert eR < 2e-5
+    assert_grad_close(G.cpu().numpy()[idx], G0, f"G ({name}, mesh repulsion)", rel=2e-4,
+                      atol=1e-5)
