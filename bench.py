@@ -58,6 +58,11 @@ def parse_args(argv=None):
                     help="direct sum (exact) or the interpolated node field of the density "
                          "(fast, approximate; the step's pairs are then counted as equivalent "
                          "pair interactions)")
+    ap.add_argument("--repulsion", choices=("direct", "mesh"), default="direct",
+                    help="every pair (exact) or the particle-particle particle-mesh summation "
+                         "(fast, approximate; pairs counted as equivalent pair interactions)")
+    ap.add_argument("--mesh-cells", type=int, default=256,
+                    help="mesh cells across the sample box for --repulsion mesh")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -67,8 +72,10 @@ def parse_args(argv=None):
         a.steps = 1 if a.workload == "hr" else 3
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if a.attraction == "field" and (a.workload == "batched" or a.path == "engine"):
-        ap.error("--attraction field runs on the kernels path (the engine takes the direct sum)")
+    if (a.attraction == "field" or a.repulsion == "mesh") and (a.workload == "batched"
+                                                               or a.path == "engine"):
+        ap.error("--attraction field / --repulsion mesh run on the kernels path "
+                 "(the engine takes the direct sums)")
     return a
 
 
@@ -322,6 +329,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     field_build_ms = None
+    mesh_build_ms = None
+    if args.repulsion == "mesh":
+        sp.sparkling_set_repulsion(ctx, sp.REPULSION_MESH, sp.make_mesh(args.mesh_cells))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        w.step()                                  # builds the kernel spectra (blocking)
+        sp.sparkling_status(ctx)
+        mesh_build_ms = (time.perf_counter() - t0) * 1e3
     if args.attraction == "field":
         sp.sparkling_set_attraction(ctx, sp.ATTRACTION_FIELD)
         torch.cuda.synchronize(dev)
@@ -377,14 +392,19 @@ def run_ours(args):
     if w.batched:
         # one engine launch runs every pair of the step: N_b*P_b + N_b*(N_b-1)
         kname, kpairs = "engine", w.pairs
-    elif args.attraction == "field":
+    elif args.repulsion == "mesh" and args.attraction == "direct":
+        p0 = w.probs[0]
+        kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
+    elif args.attraction == "field" and args.repulsion == "direct":
         # the attraction is an interpolation; the symmetric repulsion takes
         # one reciprocal square root per unordered pair
         kname, kpairs = "repulsion", w.N * (w.N - 1) // 2
+    elif args.attraction == "field":
+        kname, kpairs = None, None
     else:
         p0 = w.probs[0]
         kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
-    k_ms, k_n = ktimes[kname]
+    k_ms, k_n = ktimes[kname] if kname else (0.0, 0)
     achieved = kpairs / (k_ms / k_n * 1e-3) if k_n else None
     roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak / 1e9, "unit": "Gpair/s",
@@ -456,12 +476,18 @@ def run_ours(args):
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
                        "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
                        "l2": "flushed (512 MB write) between timed steps", "acc": args.acc,
-                       "attraction": args.attraction},
+                       "attraction": args.attraction, "repulsion": args.repulsion},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,
             "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
         }
+        if mesh_build_ms is not None:
+            out["mesh"] = {
+                "cells": args.mesh_cells, "first_step_ms": mesh_build_ms,
+                "note": "particle-particle particle-mesh repulsion (sigma 2.5 cells, cut-off 4 "
+                        "sigma); the first step builds the kernel spectra once; value counts "
+                        "N*P + N*(N-1) equivalent pairs"}
         if field_build_ms is not None:
             out["field"] = {
                 "build_ms": field_build_ms,

@@ -157,5 +157,7 @@ def test_mesh_full_size_sampled_targets(sp, name, n_cells, m):
     print(f"mesh repulsion {name} ({n_cells} cells): R rel L2 {eR:.2e}, G rel L2 {eG:.2e}, "
           f"repulsion {t['repulsion'][0]:.1f} ms (first call, with the kernel spectra)")
     assert eR < 2e-5
-    assert_grad_close(G.cpu().numpy()[idx], G0, f"G ({name}, mesh repulsion)", rel=2e-4,
-                      atol=1e-5)
+    # the attraction here is the compensated-FP32 direct sum (about 1e-5 per
+    # component at these grid sizes) and the mesh adds its own ~1e-6
+    assert_grad_close(G.cpu().numpy()[idx], G0, f"G ({name}, mesh repulsion)", rel=2e-5,
+                      atol=2e-5)
