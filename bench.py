@@ -67,6 +67,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
+    ap.add_argument("--crossover", action="store_true",
+                    help="instead of the step: time the exact (symmetric) and the mesh repulsion "
+                         "over a range of N and report where the mesh wins")
     a = ap.parse_args(argv)
     if a.steps is None:
         a.steps = 1 if a.workload == "hr" else 3
@@ -502,10 +505,61 @@ def run_ours(args):
     return 0
 
 
+def run_crossover(args):
+    """Repulsion-only timing of the exact symmetric kernel and of the mesh
+    summation (sigma 2.5 cells, cut-off 4 sigma, mesh cells growing like
+    N^(1/3), 256 at 10.5M samples) on uniform samples in [-0.45, 0.45]^3; the
+    mesh result is compared with the exact one computed on the device."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2108_02991_gb300 as sp
+    import inputs
+    dev = torch.device("cuda", 0)
+    grid = inputs.density_gaussian(8, 0.2)
+    rho = torch.from_numpy(grid.rho).to(dev)
+    g = sp.make_grid(rho, grid.lo, grid.hi, grid.n)
+    rows = []
+    for N in (10_000, 30_000, 100_000, 300_000, 1_000_000, 3_000_000):
+        K = torch.from_numpy(np.random.default_rng(N).uniform(-0.45, 0.45, size=(N, 3))
+                             .astype(np.float32)).to(dev)
+        cells = int(min(512, max(16, round(256 * (N / 10_485_760) ** (1 / 3) / 8) * 8)))
+        out = {}
+        for mode in ("direct", "mesh"):
+            ctx = sp.sparkling_create(0)
+            if mode == "mesh":
+                sp.sparkling_set_repulsion(ctx, sp.REPULSION_MESH, sp.make_mesh(cells))
+            R = torch.empty(N, 3, dtype=torch.float64, device=dev)
+            G = torch.empty_like(R)
+            for _ in range(2):                   # tuning / kernel spectra, then warm
+                sp.sparkling_grad(ctx, K, g, sp.ACC_KAHAN32, G=G, R=R)
+            sp.sparkling_status(ctx)
+            sp.sparkling_set_timing(ctx, True)
+            sp.sparkling_kernel_times(ctx, reset=True)
+            for _ in range(args.steps):
+                sp.sparkling_grad(ctx, K, g, sp.ACC_KAHAN32, G=G, R=R)
+            sp.sparkling_status(ctx)
+            ms, n = sp.sparkling_kernel_times(ctx, reset=True)["repulsion"]
+            out[mode] = (ms / n, R.clone())
+            ctx.close()
+        err = float(torch.linalg.norm(out["mesh"][1] - out["direct"][1]) /
+                    torch.linalg.norm(out["direct"][1]))
+        rows.append({"N": N, "mesh_cells": cells, "direct_ms": out["direct"][0],
+                     "mesh_ms": out["mesh"][0], "mesh_rel_l2_vs_direct": err})
+    cross = next((r["N"] for r in rows if r["mesh_ms"] < r["direct_ms"]), None)
+    print(json.dumps({"metric": "repulsion_crossover", "unit": "ms per repulsion evaluation",
+                      "rows": rows, "first_N_where_mesh_is_faster": cross,
+                      "data": "synthetic: uniform samples in [-0.45, 0.45]^3"}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.crossover:
+        return run_crossover(args)
     return run_ours(args)
 
 

@@ -367,7 +367,9 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
  *     by the caller.  The kernel spectra are built at the first call that
  *     needs them (blocking, about 100 L^3 bytes of temporary device memory,
  *     L = 4 (n_cells + 2g)), again when the mesh or the regularisation
- *     changes.  A sample outside the mesh gives SPARKLING_E_RANGE.
+ *     changes.  A sample outside the mesh gives SPARKLING_E_RANGE.  Each
+ *     evaluation reads the size of its short-range work list back to the
+ *     host (one stream synchronisation), so it cannot be stream-captured.
  * Returns SPARKLING_E_INVAL for a bad mode or mesh. */
 SPARKLING_API int sparkling_set_repulsion(sparkling_ctx *ctx, int mode, const sparkling_mesh *mesh);
 

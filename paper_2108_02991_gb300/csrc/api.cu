@@ -618,6 +618,11 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     if (mesh_mode) {
         int s;
         if ((s = ensure_mesh(ctx, st))) return s;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(ctx, SPARKLING_E_INVAL,
+                        "the mesh repulsion reads its work size back and cannot be captured");
         r_direct = at<dacc4>(ctx, P.o_rdir);
         const char *what = "";
         int nk = 0;

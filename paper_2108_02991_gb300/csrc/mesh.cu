@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -211,17 +212,23 @@ __global__ void spectrum_product_kernel(cufftComplex *out, const cufftComplex *_
     }
 }
 
-// Long-range sums gathered from the four convolved fields (L^3 boxes; node n
-// of the mesh is box index n), plus the short-range sums: out = S + L.
+// Long-range sums gathered from the convolved fields (L^3 boxes; node n of
+// the mesh is box index n) -- the force x, y, z fields, or the potential
+// field alone for the energy -- plus the short-range fixed-point sums
+// ([N][3] or [N][1]): out = S + L.
+template <bool ENERGY>
 __global__ void gather_kernel(const float4 *__restrict__ pos, int64_t N,
                               const float *__restrict__ phi, int64_t box, int L, double x0,
-                              double inv_h, int M, int ncomp, const dacc4 *__restrict__ shortr,
+                              double inv_h, int M, const unsigned long long *__restrict__ shortr,
                               dacc4 *out)
 {
+    constexpr int NC = ENERGY ? 1 : 3;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const NodeWeights nw = node_weights(pos[i], x0, inv_h, M);
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] = 0.f;
         if (nw.ok) {
             for (int c = 0; c < 4; ++c)
                 for (int b = 0; b < 4; ++b) {
@@ -231,17 +238,22 @@ __global__ void gather_kernel(const float4 *__restrict__ pos, int64_t N,
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const float w = wzy * nw.w[0][a];
-                        for (int k = 0; k < ncomp; ++k)
+#pragma unroll
+                        for (int k = 0; k < NC; ++k)
                             acc[k] = fmaf(w, __ldg(phi + k * box + row + a), acc[k]);
                     }
                 }
         }
-        const dacc4 s = shortr[i];
         dacc4 r;
-        r.x = s.x + (double)acc[0];
-        r.y = s.y + (double)acc[1];
-        r.z = s.z + (double)acc[2];
-        r.w = s.w + (double)acc[3];
+        if (ENERGY) {
+            r.x = r.y = r.z = 0.0;
+            r.w = (double)(long long)shortr[i] * (1.0 / kFix) + (double)acc[0];
+        } else {
+            r.x = (double)(long long)shortr[3 * i] * (1.0 / kFix) + (double)acc[0];
+            r.y = (double)(long long)shortr[3 * i + 1] * (1.0 / kFix) + (double)acc[NC > 1 ? 1 : 0];
+            r.z = (double)(long long)shortr[3 * i + 2] * (1.0 / kFix) + (double)acc[NC > 2 ? 2 : 0];
+            r.w = 0.0;
+        }
         out[i] = r;
     }
 }
@@ -295,61 +307,169 @@ __device__ __forceinline__ float erfc_as(float x, float &gauss)
     return t * poly * gauss;
 }
 
-// One thread per sample in cell order: the short-range sums over the 27
-// cells around the sample's cell, pairs with |d| < rc.  The self pair adds
-// nothing to the force and g_short(0) to the potential.
-template <bool ENERGY>
-__global__ void __launch_bounds__(kMeshThreads) short_kernel(
-    const float4 *__restrict__ spos, const int *__restrict__ idx, const int *__restrict__ start,
-    const int *__restrict__ end, int64_t N, int nc, float x0, float inv_cs, float rc2,
-    float inv_sigma, float spi, float eps2, dacc4 *out)
+// Sorted range [j0, j1) of the sources in row r (0..8: dz, dy in -1..1) of
+// the 3 x 3 x 3 cells around cell (cx, cy, cz): the three x-neighbours of a
+// row are consecutive cells, so their samples are one contiguous range.
+__device__ __forceinline__ bool row_range(int cx, int cy, int cz, int r, int nc,
+                                          const int *__restrict__ start,
+                                          const int *__restrict__ end, int &j0, int &j1)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const float4 p = spos[k];
-        const int cx = cell_coord(p.x, x0, inv_cs, nc), cy = cell_coord(p.y, x0, inv_cs, nc),
-                  cz = cell_coord(p.z, x0, inv_cs, nc);
-        double sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = cz + dz;
-            if (z < 0 || z >= nc) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = cy + dy;
-                if (y < 0 || y >= nc) continue;
-                // the three x-neighbours are consecutive cells: one range
-                const int xa = cx > 0 ? cx - 1 : 0, xb = cx < nc - 1 ? cx + 1 : nc - 1;
-                const int base = (z * nc + y) * nc;
-                int j0 = -1, j1 = -1;
-                for (int x = xa; x <= xb; ++x) {
-                    const int s = start[base + x], e = end[base + x];
-                    if (s < e) {
-                        if (j0 < 0) j0 = s;
-                        j1 = e;
-                    }
-                }
-                if (j0 < 0) continue;
-                float fx = 0.f, fy = 0.f, fz = 0.f, fe = 0.f;
-                for (int j = j0; j < j1; ++j) {
-                    const float4 q = spos[j];
-                    const float ddx = p.x - q.x, ddy = p.y - q.y, ddz = p.z - q.z;
-                    const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                    if (d2 < rc2) {
-                        const float re2 = d2 + eps2;
-                        const float ri = rsqrt_sfu(fmaxf(re2, kEps2));
-                        const float r = re2 * ri;
-                        float gauss;
-                        const float ec = erfc_as(r * inv_sigma, gauss);
-                        const float w = ec * ri;
-                        fx = fmaf(ddx, w, fx);
-                        fy = fmaf(ddy, w, fy);
-                        fz = fmaf(ddz, w, fz);
-                        if (ENERGY) fe += fmaf(r, ec, -spi * gauss);
-                    }
-                }
-                sx += fx; sy += fy; sz += fz; se += fe;
+    const int z = cz + r / 3 - 1, y = cy + r % 3 - 1;
+    if (z < 0 || z >= nc || y < 0 || y >= nc) return false;
+    const int xa = cx > 0 ? cx - 1 : 0, xb = cx < nc - 1 ? cx + 1 : nc - 1;
+    const int base = (z * nc + y) * nc;
+    j0 = -1;
+    for (int x = xa; x <= xb; ++x) {
+        const int s = start[base + x], e = end[base + x];
+        if (s < e) {
+            if (j0 < 0) j0 = s;
+            j1 = e;
+        }
+    }
+    return j0 >= 0;
+}
+
+constexpr int kShortThreads = 128;
+constexpr int kShortChunk = 2 * kShortThreads;   // targets per item (2 per thread)
+constexpr int kShortSlice = 8192;                // sources per item at most
+constexpr int kShortTile = 1024;                 // sources per shared-memory tile
+
+// Items of cell c: ceil(n_c / kShortChunk) target chunks times the source
+// slices of its 9 rows.
+__global__ void count_items_kernel(const int *__restrict__ start, const int *__restrict__ end,
+                                   int nc, int *counts, int *slices)
+{
+    const int ncell = nc * nc * nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int n = end[c] - start[c];
+        int cnt = 0, sl = 0;
+        if (n > 0) {
+            const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+            for (int r = 0; r < 9; ++r) {
+                int j0, j1;
+                if (row_range(cx, cy, cz, r, nc, start, end, j0, j1))
+                    sl += (j1 - j0 + kShortSlice - 1) / kShortSlice;
+            }
+            cnt = ((n + kShortChunk - 1) / kShortChunk) * sl;
+        }
+        counts[c] = cnt;
+        slices[c] = sl;
+    }
+}
+
+// Item u -> (targets t0, tn; sources s0, sn), all sorted positions.
+__global__ void fill_items_kernel(const int *__restrict__ offsets, const int *__restrict__ slices,
+                                  const int *__restrict__ start, const int *__restrict__ end,
+                                  int nc, int64_t total, int4 *items)
+{
+    const int ncell = nc * nc * nc;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ncell - 1;            // largest c with offsets[c] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)offsets[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const int c = lo;
+        const int local = (int)(u - offsets[c]), sl = slices[c];
+        const int k = local / sl;
+        int rs = local % sl;
+        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+        int4 it = make_int4(start[c] + k * kShortChunk, 0, 0, 0);
+        it.y = min(kShortChunk, end[c] - it.x);
+        for (int r = 0; r < 9; ++r) {
+            int j0, j1;
+            if (!row_range(cx, cy, cz, r, nc, start, end, j0, j1)) continue;
+            const int ns = (j1 - j0 + kShortSlice - 1) / kShortSlice;
+            if (rs < ns) {
+                it.z = j0 + rs * kShortSlice;
+                it.w = min(kShortSlice, j1 - it.z);
+                break;
+            }
+            rs -= ns;
+        }
+        items[u] = it;
+    }
+}
+
+// Short-range pair term of target p and source q, added to f (force) or
+// f[0] (energy): pairs with |d| < rc only; the self pair adds nothing to the
+// force and g_short(0) to the energy.
+template <bool ENERGY>
+__device__ __forceinline__ void short_pair(const float4 p, const float4 q, float rc2,
+                                           float inv_sigma, float spi, float eps2, float *f)
+{
+    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 < rc2) {
+        const float re2 = d2 + eps2;
+        const float ri = rsqrt_sfu(fmaxf(re2, kEps2));
+        const float r = re2 * ri;
+        float gauss;
+        const float ec = erfc_as(r * inv_sigma, gauss);
+        if (ENERGY) {
+            f[0] += fmaf(r, ec, -spi * gauss);
+        } else {
+            const float w = ec * ri;
+            f[0] = fmaf(dx, w, f[0]);
+            f[1] = fmaf(dy, w, f[1]);
+            f[2] = fmaf(dz, w, f[2]);
+        }
+    }
+}
+
+// Persistent CTAs take items from a queue: kShortChunk targets of one cell
+// (two per thread) against up to kShortSlice sources of one neighbour row,
+// staged through shared memory in tiles; the item sums are added to the
+// targets' 64-bit fixed-point accumulators (exact, order-free).
+template <bool ENERGY>
+__global__ void __launch_bounds__(kShortThreads) short_items_kernel(
+    const int4 *__restrict__ items, const int *__restrict__ n_items, unsigned int *queue,
+    const float4 *__restrict__ spos, const int *__restrict__ idx, float rc2, float inv_sigma,
+    float spi, float eps2, unsigned long long *acc)
+{
+    constexpr int NV = ENERGY ? 1 : 3;
+    __shared__ float4 src[kShortTile];
+    __shared__ int item_id;
+    const int tid = threadIdx.x;
+    const int total = *n_items;
+    for (;;) {
+        if (tid == 0) item_id = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int u = item_id;
+        __syncthreads();
+        if (u >= total) break;
+        const int4 it = items[u];
+        float4 p[2];
+        bool ok[2];
+        float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        for (int t = 0; t < 2; ++t) {
+            const int l = tid + t * kShortThreads;
+            ok[t] = l < it.y;
+            p[t] = ok[t] ? spos[it.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int b = 0; b < it.w; b += kShortTile) {
+            const int cnt = min(kShortTile, it.w - b);
+            for (int e = tid; e < cnt; e += kShortThreads) src[e] = spos[it.z + b + e];
+            __syncthreads();
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = src[j];
+                short_pair<ENERGY>(p[0], q, rc2, inv_sigma, spi, eps2, f[0]);
+                short_pair<ENERGY>(p[1], q, rc2, inv_sigma, spi, eps2, f[1]);
+            }
+            __syncthreads();
+        }
+        for (int t = 0; t < 2; ++t) {
+            if (!ok[t]) continue;
+            unsigned long long *a = acc + (int64_t)idx[it.x + tid + t * kShortThreads] * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const long long x = __float2ll_rn(f[t][v] * 4294967296.0f);
+                if (x) atomicAdd(a + v, (unsigned long long)x);
             }
         }
-        out[idx[k]] = make_dacc4(sx, sy, sz, se);
     }
 }
 
@@ -397,7 +517,12 @@ struct MeshState {
     int *vals = nullptr; size_t vals_cap = 0;
     int *ranges = nullptr; size_t ranges_cap = 0;        // start[nc^3], end[nc^3]
     float4 *spos = nullptr; size_t spos_cap = 0;
-    dacc4 *shortr = nullptr; size_t shortr_cap = 0;
+    unsigned long long *shortr = nullptr; size_t shortr_cap = 0;   // fixed point [N][3]
+    int *cellwork = nullptr; size_t cellwork_cap = 0;   // counts, slices, offsets [ncell] each
+    int4 *items = nullptr; size_t items_cap = 0;
+    int *small = nullptr;                               // n_items, queue
+    int short_ctas[2] = {0, 0};                         // persistent CTAs (gradient, energy)
+    int host_small[2] = {0, 0};                         // source of the n_items / queue upload
     void *cub = nullptr; size_t cub_cap = 0;
 };
 
@@ -409,7 +534,8 @@ void mesh_state_destroy(MeshState *m)
     if (m->plans) { cufftDestroy(m->r2c); cufftDestroy(m->c2r); }
     cudaFree(m->spectra); cudaFree(m->Q); cudaFree(m->box); cudaFree(m->qhat); cudaFree(m->tmp);
     cudaFree(m->keys); cudaFree(m->vals); cudaFree(m->ranges); cudaFree(m->spos);
-    cudaFree(m->shortr); cudaFree(m->cub);
+    cudaFree(m->shortr); cudaFree(m->cub); cudaFree(m->cellwork); cudaFree(m->items);
+    cudaFree(m->small);
     delete m;
 }
 
@@ -525,74 +651,115 @@ cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t 
 
 // Repulsion sums of the N packed samples into out[i] = (sum d/r, sum |d|_eps)
 // over all j (directed, the self pair included as eps in the potential).
+// Reads the number of short-range work items back to the host (one sync).
 cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, dacc4 *out,
                       int *status, int sms, cudaStream_t st, const char **what, int *launches)
 {
     const MeshConfig &c = m->cfg;
     const int M = m->M, L = m->L, nc = m->nc;
     const int64_t nm = (int64_t)M * M * M, nl = (int64_t)L * L * L, nlc = (int64_t)L * L * (L / 2 + 1);
-    const int ncomp = energy ? 4 : 3;
-    const int64_t ncell = (int64_t)nc * nc * nc;
+    const int nfield = energy ? 1 : 3;
+    const int NV = energy ? 1 : 3;
+    const int ncell = nc * nc * nc;
     const double h = (c.hi - c.lo) / c.n_cells;
     cudaError_t err;
     *what = "mesh evaluation buffers";
-    size_t cub_bytes = 0;
+    size_t sort_bytes = 0, scan_bytes = 0;
     int end_bit = 1;
     while (((int64_t)1 << end_bit) < ncell) ++end_bit;
-    cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, m->keys, m->keys, m->vals, m->vals,
+    cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, m->keys, m->keys, m->vals, m->vals,
                                     (int)N, 0, end_bit, st);
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, m->cellwork, m->cellwork, ncell, st);
+    const size_t cub_bytes = std::max(sort_bytes, scan_bytes);
     if ((err = grow(m->Q, m->Q_cap, nm * sizeof(unsigned long long))) ||
-        (err = grow(m->box, m->box_cap, (size_t)(ncomp + 1) * nl * sizeof(float))) ||
+        (err = grow(m->box, m->box_cap, (size_t)(nfield + 1) * nl * sizeof(float))) ||
         (err = grow(m->qhat, m->qhat_cap, nlc * sizeof(cufftComplex))) ||
         (err = grow(m->tmp, m->tmp_cap, nlc * sizeof(cufftComplex))) ||
         (err = grow(m->keys, m->keys_cap, (size_t)2 * N * sizeof(unsigned int))) ||
         (err = grow(m->vals, m->vals_cap, (size_t)2 * N * sizeof(int))) ||
         (err = grow(m->ranges, m->ranges_cap, (size_t)2 * ncell * sizeof(int))) ||
         (err = grow(m->spos, m->spos_cap, (size_t)N * sizeof(float4))) ||
-        (err = grow(m->shortr, m->shortr_cap, (size_t)N * sizeof(dacc4))) ||
+        (err = grow(m->shortr, m->shortr_cap, (size_t)N * 3 * sizeof(unsigned long long))) ||
+        (err = grow(m->cellwork, m->cellwork_cap, (size_t)3 * ncell * sizeof(int))) ||
         (err = grow(m->cub, m->cub_cap, cub_bytes + 256)))
         return err;
+    if (!m->small && (err = cudaMalloc(&m->small, 4 * sizeof(int)))) return err;
+    if (!m->short_ctas[0]) {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, short_items_kernel<false>, kShortThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, short_items_kernel<true>, kShortThreads, 0);
+        m->short_ctas[0] = sms * std::max(a, 1);
+        m->short_ctas[1] = sms * std::max(b, 1);
+    }
     if (cufftSetStream(m->r2c, st) != CUFFT_SUCCESS || cufftSetStream(m->c2r, st) != CUFFT_SUCCESS)
         return cudaErrorUnknown;
     *what = "mesh evaluation";
-    const int gN = grid_for(N, sms);
-    // short-range part: cell list sorted by cell, then the pair sums
+    const int gN = grid_for(N, sms), gC = grid_for(ncell, sms);
+    int nk = 0;
+    // short-range part: samples sorted by cell, work items, pair sums
     const float cs = (float)(M * h / nc);
     cell_keys_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, (float)m->x0, 1.f / cs, nc, m->keys,
                                                   m->vals);
-    if ((err = cub::DeviceRadixSort::SortPairs(m->cub, cub_bytes, m->keys, m->keys + N, m->vals,
+    if ((err = cub::DeviceRadixSort::SortPairs(m->cub, sort_bytes, m->keys, m->keys + N, m->vals,
                                                m->vals + N, (int)N, 0, end_bit, st)))
         return err;
     if ((err = cudaMemsetAsync(m->ranges, 0, (size_t)2 * ncell * sizeof(int), st))) return err;
-    cell_ranges_kernel<<<gN, kMeshThreads, 0, st>>>(m->keys + N, m->vals + N, pos, N, m->ranges,
-                                                    m->ranges + ncell, m->spos);
+    int *start = m->ranges, *end = m->ranges + ncell;
+    cell_ranges_kernel<<<gN, kMeshThreads, 0, st>>>(m->keys + N, m->vals + N, pos, N, start, end,
+                                                    m->spos);
+    int *counts = m->cellwork, *slices = counts + ncell, *offsets = slices + ncell;
+    count_items_kernel<<<gC, kMeshThreads, 0, st>>>(start, end, nc, counts, slices);
+    if ((err = cub::DeviceScan::ExclusiveSum(m->cub, scan_bytes, counts, offsets, ncell, st)))
+        return err;
+    int h2[2];
+    if ((err = cudaMemcpyAsync(&h2[0], offsets + ncell - 1, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        (err = cudaMemcpyAsync(&h2[1], counts + ncell - 1, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        (err = cudaStreamSynchronize(st)))
+        return err;
+    const int64_t total = (int64_t)h2[0] + h2[1];
+    if (total > ((int64_t)1 << 31) - 1) return cudaErrorInvalidValue;
+    if ((err = grow(m->items, m->items_cap, (size_t)std::max<int64_t>(total, 1) * sizeof(int4))))
+        return err;
+    m->host_small[0] = (int)total;
+    m->host_small[1] = 0;
+    if ((err = cudaMemcpyAsync(m->small, m->host_small, 2 * sizeof(int), cudaMemcpyHostToDevice, st)))
+        return err;
+    if (total > 0)
+        fill_items_kernel<<<grid_for(total, sms), kMeshThreads, 0, st>>>(offsets, slices, start,
+                                                                         end, nc, total, m->items);
+    if ((err = cudaMemsetAsync(m->shortr, 0, (size_t)N * NV * sizeof(unsigned long long), st)))
+        return err;
     const float rc2 = (float)(c.rc * c.rc), inv_sigma = (float)(1.0 / c.sigma);
     const float spi = (float)(c.sigma * 0.56418958354775628);
     const float eps2 = (float)(c.eps * c.eps);
+    unsigned int *queue = reinterpret_cast<unsigned int *>(m->small + 1);
     if (energy)
-        short_kernel<true><<<gN, kMeshThreads, 0, st>>>(m->spos, m->vals + N, m->ranges,
-                                                        m->ranges + ncell, N, nc, (float)m->x0,
-                                                        1.f / cs, rc2, inv_sigma, spi, eps2,
-                                                        m->shortr);
+        short_items_kernel<true><<<m->short_ctas[1], kShortThreads, 0, st>>>(
+            m->items, m->small, queue, m->spos, m->vals + N, rc2, inv_sigma, spi, eps2, m->shortr);
     else
-        short_kernel<false><<<gN, kMeshThreads, 0, st>>>(m->spos, m->vals + N, m->ranges,
-                                                         m->ranges + ncell, N, nc, (float)m->x0,
-                                                         1.f / cs, rc2, inv_sigma, spi, eps2,
-                                                         m->shortr);
+        short_items_kernel<false><<<m->short_ctas[0], kShortThreads, 0, st>>>(
+            m->items, m->small, queue, m->spos, m->vals + N, rc2, inv_sigma, spi, eps2, m->shortr);
+    nk += 6;
     // long-range part
     if ((err = cudaMemsetAsync(m->Q, 0, nm * sizeof(unsigned long long), st))) return err;
     spread_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, m->Q, m->x0, 1.0 / h, M, status);
     charges_to_box_kernel<<<grid_for(nl, sms), kMeshThreads, 0, st>>>(m->Q, m->box, M, L);
     if (cufftExecR2C(m->r2c, m->box, m->qhat) != CUFFT_SUCCESS) return cudaErrorUnknown;
-    for (int k = 0; k < ncomp; ++k) {
+    for (int k = 0; k < nfield; ++k) {
+        const int comp = energy ? 3 : k;
         spectrum_product_kernel<<<grid_for(nlc, sms), kMeshThreads, 0, st>>>(
-            m->tmp, m->qhat, m->spectra + k * nlc, nlc);
+            m->tmp, m->qhat, m->spectra + comp * nlc, nlc);
         if (cufftExecC2R(m->c2r, m->tmp, m->box + (1 + k) * nl) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
     }
-    gather_kernel<<<gN, kMeshThreads, 0, st>>>(pos, N, m->box + nl, nl, L, m->x0, 1.0 / h, M, ncomp,
-                                               m->shortr, out);
-    *launches = 8 + 2 * ncomp;
+    if (energy)
+        gather_kernel<true><<<gN, kMeshThreads, 0, st>>>(pos, N, m->box + nl, nl, L, m->x0,
+                                                         1.0 / h, M, m->shortr, out);
+    else
+        gather_kernel<false><<<gN, kMeshThreads, 0, st>>>(pos, N, m->box + nl, nl, L, m->x0,
+                                                          1.0 / h, M, m->shortr, out);
+    nk += 3 + nfield + 1;
+    *launches = nk;
     *what = "";
     return cudaGetLastError();
 }
