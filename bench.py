@@ -63,6 +63,10 @@ def parse_args(argv=None):
                          "(fast, approximate; pairs counted as equivalent pair interactions)")
     ap.add_argument("--mesh-cells", type=int, default=256,
                     help="mesh cells across the sample box for --repulsion mesh")
+    ap.add_argument("--mesh-sigma", type=float, default=2.5,
+                    help="split width in mesh cells for --repulsion mesh")
+    ap.add_argument("--mesh-rc", type=float, default=4.0,
+                    help="short-range cut-off in split widths for --repulsion mesh")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -334,7 +338,8 @@ def run_ours(args):
     field_build_ms = None
     mesh_build_ms = None
     if args.repulsion == "mesh":
-        sp.sparkling_set_repulsion(ctx, sp.REPULSION_MESH, sp.make_mesh(args.mesh_cells))
+        sp.sparkling_set_repulsion(ctx, sp.REPULSION_MESH,
+                                   sp.make_mesh(args.mesh_cells, args.mesh_sigma, args.mesh_rc))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         w.step()                                  # builds the kernel spectra (blocking)
@@ -487,10 +492,10 @@ def run_ours(args):
         }
         if mesh_build_ms is not None:
             out["mesh"] = {
-                "cells": args.mesh_cells, "first_step_ms": mesh_build_ms,
-                "note": "particle-particle particle-mesh repulsion (sigma 2.5 cells, cut-off 4 "
-                        "sigma); the first step builds the kernel spectra once; value counts "
-                        "N*P + N*(N-1) equivalent pairs"}
+                "cells": args.mesh_cells, "sigma_cells": args.mesh_sigma,
+                "rc_sigmas": args.mesh_rc, "first_step_ms": mesh_build_ms,
+                "note": "particle-particle particle-mesh repulsion; the first step builds the "
+                        "kernel spectra once; value counts N*P + N*(N-1) equivalent pairs"}
         if field_build_ms is not None:
             out["field"] = {
                 "build_ms": field_build_ms,

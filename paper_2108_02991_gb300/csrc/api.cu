@@ -66,6 +66,10 @@ struct sparkling_ctx {
         std::vector<EngineItem> items;
         std::vector<size_t> o_rho, o_coords;
         size_t o_pos = 0, o_traj = 0, o_items = 0, o_cnt = 0, o_part = 0, o_gstate = 0, end = 0;
+        bool sym = false;                 // repulsion by the batched symmetric kernel
+        size_t o_racc = 0, o_symtraj = 0;
+        int64_t sym_units = 0;
+        std::vector<SymTraj> symtraj;
         bool proj_in_smem = false;
         int64_t kernels_per_step = 0;
         // graph of the device work of one step (counters, packs, engine)
@@ -797,13 +801,14 @@ int64_t pair_cost(int64_t N, int64_t P) { return N * P + N * N; }
 // shot.  Attraction and repulsion items alternate so that neighbouring CTAs
 // (and hence the CTAs resident on one SM) mix SFU-bound and issue-bound work.
 void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
-                     const sparkling_grid *grids, int ctas, int items_per_cta)
+                     const sparkling_grid *grids, int ctas, int items_per_cta, bool sym)
 {
     const int B = (int)off.size() - 1;
     int64_t total = 0;
     for (int t = 0; t < B; ++t) {
         const int64_t P = (int64_t)grids[t].n[0] * grids[t].n[1] * grids[t].n[2];
-        total += pair_cost(off[t + 1] - off[t], P);
+        const int64_t N = off[t + 1] - off[t];
+        total += sym ? N * P : pair_cost(N, P);
     }
     const double target = (double)total / ((double)ctas * items_per_cta);
     b.traj.assign(B, EngineTraj());
@@ -821,7 +826,8 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
         rc = rc < 1 ? 1 : (rc > rows ? rows : rc);
         int64_t sc = (int64_t)(target / ((double)kTile * kSrcBlock) + 0.5);
         sc = sc < 1 ? 1 : (sc > blocks ? blocks : sc);
-        const int ach = (int)((rows + rc - 1) / rc), rch = (int)((blocks + sc - 1) / sc);
+        const int ach = (int)((rows + rc - 1) / rc);
+        const int rch = sym ? 0 : (int)((blocks + sc - 1) / sc);   // sym: a separate kernel
         tr.off = off[t];
         tr.N = N;
         tr.Ns = b.Ns;
@@ -935,6 +941,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
     e.status = ctx->d_status;
     e.eps2 = eps2_of(ctx);
+    e.racc = b.sym ? at<unsigned long long>(ctx, b.o_racc) : nullptr;
     const int ctas = ctx->sms * engine_ctas_per_sm(acc, K_dtype, variant);
     CK(launch_engine(e, acc, K_dtype, variant, std::min(ctas, b.ctas), st));
     return SPARKLING_OK;
@@ -946,7 +953,26 @@ int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_
 {
     int s;
     if ((s = batch_pack(ctx, K, K_dtype, grids, st))) return s;
-    return batch_engine(ctx, K, K_dtype, acc, variant, (int64_t)ctx->batch.items.size(), st);
+    sparkling_ctx::Batch &b = ctx->batch;
+    if (b.sym) {
+        // every unordered pair of every trajectory once, fixed-point totals
+        unsigned long long *racc = at<unsigned long long>(ctx, b.o_racc);
+        CK(cudaMemsetAsync(racc, 0, (size_t)b.off[b.B] * 3 * sizeof(unsigned long long), st));
+        SymArgs sa{};
+        sa.pos = at<float4>(ctx, b.o_pos);
+        sa.N = b.off[b.B];
+        sa.tiles = 0;
+        sa.acc = racc;
+        sa.status = ctx->d_status;
+        sa.eps2 = eps2_of(ctx);
+        sa.traj = at<SymTraj>(ctx, b.o_symtraj);
+        sa.B = b.B;
+        sa.units = b.sym_units;
+        const int sv = ctx->sym_choice < 0 ? 0 : ctx->sym_choice;
+        sa.ctas = std::min<int64_t>((int64_t)ctx->sms * ctx->occ_sym[0][sv], b.sym_units);
+        CK(launch_repulsion_sym(sa, false, sv, st));
+    }
+    return batch_engine(ctx, K, K_dtype, acc, variant, (int64_t)b.items.size(), st);
 }
 
 // Engine autotuner: time each tile shape on a prefix of the pair items (about
@@ -1351,6 +1377,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     int s;
     if ((s = validate_batch(ctx, B, traj_off, K, K_dtype, Ns, grids, eta, proj, acc))) return s;
     if ((s = lazy_init(ctx))) return s;
+    if ((s = ensure_occupancy(ctx))) return s;
     if (!is_device_ptr(K)) return fail(ctx, SPARKLING_E_INVAL, "K must be device memory");
     for (int t = 0; t < B; ++t)
         if (!is_device_ptr(grids[t].rho))
@@ -1375,7 +1402,8 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         b.B = B; b.Ns = Ns; b.acc = acc; b.dtype = K_dtype; b.ctas = ctas;
         b.items_per_cta = ctx->items_per_cta;
         b.off = off; b.dims = dims;
-        build_work_list(b, off, grids, ctas, ctx->items_per_cta);
+        b.sym = ctx->rep_symmetric;
+        build_work_list(b, off, grids, ctas, ctx->items_per_cta, b.sym);
         Carve cv;
         b.o_pos = cv.take((size_t)off[B] * sizeof(float4));
         for (int t = 0; t < B; ++t) {
@@ -1390,11 +1418,29 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         b.o_part = cv.take((size_t)parts * kTile * sizeof(dacc4));
         b.proj_in_smem = project_state_bytes(Ns) <= engine_proj_smem_limit();
         if (!b.proj_in_smem) b.o_gstate = cv.take((size_t)ctas * project_state_bytes(Ns));
+        if (b.sym) {
+            b.o_racc = cv.take((size_t)off[B] * 3 * sizeof(unsigned long long));
+            b.o_symtraj = cv.take((size_t)B * sizeof(SymTraj));
+            int64_t u = 0;
+            for (int t = 0; t < B; ++t) {
+                SymTraj q;
+                q.off = off[t];
+                q.N = off[t + 1] - off[t];
+                q.tiles = (q.N + kTile - 1) / kTile;
+                q.unit0 = u;
+                u += tri_count(q.tiles);
+                b.symtraj.push_back(q);
+            }
+            b.sym_units = u;
+        }
         b.end = cv.off;
-        b.kernels_per_step = 2 + B;   // pack positions, B grid packs, engine
+        b.kernels_per_step = 2 + B + (b.sym ? 1 : 0);   // packs, (symmetric repulsion), engine
         if ((s = ensure_ws(ctx, b.end))) { b.valid = false; return s; }
         CK(cudaMemcpyAsync(at<EngineItem>(ctx, b.o_items), b.items.data(),
                            b.items.size() * sizeof(EngineItem), cudaMemcpyHostToDevice, st));
+        if (b.sym)
+            CK(cudaMemcpyAsync(at<SymTraj>(ctx, b.o_symtraj), b.symtraj.data(),
+                               (size_t)B * sizeof(SymTraj), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         b.valid = true;
     }

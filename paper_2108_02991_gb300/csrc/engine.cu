@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
                     if (s < ach) { g[0] += xy.x; g[1] += xy.y; g[2] += zz; }
                     else { r[0] += xy.x; r[1] += xy.y; r[2] += zz; }
                 }
+                if (e.racc) {   // symmetric repulsion totals (fixed point), written before the launch
+                    const unsigned long long *q = e.racc + 3 * (tr.off + i);
+                    for (int c = 0; c < 3; ++c) r[c] = (double)(long long)__ldcg(q + c) / kFixScale;
+                }
                 for (int c = 0; c < 3; ++c)
                     kv[c] = (double)K[3 * m + c] - eta * (g[c] - r[c] * invN);
             };

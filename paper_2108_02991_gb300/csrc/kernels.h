@@ -93,12 +93,21 @@ __host__ __device__ inline void tri_pair(int64_t u, int64_t T, int64_t &I, int64
 // is kept as round(x * 2^32) in an int64 (exact, order-independent addition).
 constexpr double kFixScale = 4294967296.0;
 
+// One trajectory of a batched symmetric repulsion: samples [off, off + N)
+// of pos / acc, its tiles and the first global unit of its triangle.
+struct SymTraj {
+    int64_t off, N, tiles, unit0;
+};
+
 struct SymArgs {
-    const float4 *pos;          // packed samples [N]
+    const float4 *pos;          // packed samples [N] (all trajectories when traj is set)
     int64_t N;
     int64_t tiles;              // ceil(N / kTile)
-    int64_t ctas;               // persistent CTAs; tri_count(tiles) units split evenly
+    int64_t ctas;               // persistent CTAs; the units are split evenly
     unsigned long long *acc;    // [N][NV] fixed-point sums (zeroed before the launch)
+    const SymTraj *traj = nullptr;   // batched: B trajectories (device), else one (N, tiles)
+    int32_t B = 1;
+    int64_t units = 0;          // batched: total units of all triangles
     float eps2 = kEps2;         // kernel sqrt(r^2 + eps^2): eps^2 (>= kEps2) added to every r^2
     int *status;
 };
@@ -269,6 +278,7 @@ struct EngineArgs {
     unsigned int *queue;     // next item (reset to 0 before every launch)
     unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
     double *gstate;          // per-CTA projection state when it is not in shared memory
+    const unsigned long long *racc = nullptr;   // symmetric repulsion sums [sum N][3], or null
     float eps2 = kEps2;      // eps^2 (>= kEps2) added to every r^2
     int *status;
 };

@@ -5,7 +5,7 @@
 // The kernel splits exactly: d/r = d/r erfc(r/sigma) + d/r erf(r/sigma),
 // r = |d|_eps.  The short-range part decays like a Gaussian and is summed
 // directly over the pairs closer than rc, found through a cell list (cells
-// of side >= rc, samples sorted by cell).  The long-range part is smooth and
+// of side >= rc/2, samples sorted by cell).  The long-range part is smooth and
 // is summed on a mesh:
 //   1. every sample spreads a unit charge to 4 x 4 x 4 nodes with cubic
 //      B-spline weights (64-bit fixed-point atomics: exact, order-free);
@@ -307,16 +307,25 @@ __device__ __forceinline__ float erfc_as(float x, float &gauss)
     return t * poly * gauss;
 }
 
-// Sorted range [j0, j1) of the sources in row r (0..8: dz, dy in -1..1) of
-// the 3 x 3 x 3 cells around cell (cx, cy, cz): the three x-neighbours of a
-// row are consecutive cells, so their samples are one contiguous range.
+// Cells have side >= rc / kCellReach, so the pairs closer than rc lie in the
+// (2 kCellReach + 1)^3 cells around a sample's cell (smaller cells: fewer
+// candidate pairs beyond rc).
+constexpr int kCellReach = 2;
+constexpr int kRowSpan = 2 * kCellReach + 1;
+constexpr int kRows = kRowSpan * kRowSpan;
+
+// Sorted range [j0, j1) of the sources in row r (0 .. kRows-1: dz, dy in
+// -kCellReach .. kCellReach) of the cells around cell (cx, cy, cz): the
+// x-neighbours of a row are consecutive cells, so their samples are one
+// contiguous range.
 __device__ __forceinline__ bool row_range(int cx, int cy, int cz, int r, int nc,
                                           const int *__restrict__ start,
                                           const int *__restrict__ end, int &j0, int &j1)
 {
-    const int z = cz + r / 3 - 1, y = cy + r % 3 - 1;
+    const int z = cz + r / kRowSpan - kCellReach, y = cy + r % kRowSpan - kCellReach;
     if (z < 0 || z >= nc || y < 0 || y >= nc) return false;
-    const int xa = cx > 0 ? cx - 1 : 0, xb = cx < nc - 1 ? cx + 1 : nc - 1;
+    const int xa = cx >= kCellReach ? cx - kCellReach : 0;
+    const int xb = cx < nc - kCellReach ? cx + kCellReach : nc - 1;
     const int base = (z * nc + y) * nc;
     j0 = -1;
     for (int x = xa; x <= xb; ++x) {
@@ -335,7 +344,7 @@ constexpr int kShortSlice = 8192;                // sources per item at most
 constexpr int kShortTile = 1024;                 // sources per shared-memory tile
 
 // Items of cell c: ceil(n_c / kShortChunk) target chunks times the source
-// slices of its 9 rows.
+// slices of its kRows rows.
 __global__ void count_items_kernel(const int *__restrict__ start, const int *__restrict__ end,
                                    int nc, int *counts, int *slices)
 {
@@ -345,7 +354,7 @@ __global__ void count_items_kernel(const int *__restrict__ start, const int *__r
         int cnt = 0, sl = 0;
         if (n > 0) {
             const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-            for (int r = 0; r < 9; ++r) {
+            for (int r = 0; r < kRows; ++r) {
                 int j0, j1;
                 if (row_range(cx, cy, cz, r, nc, start, end, j0, j1))
                     sl += (j1 - j0 + kShortSlice - 1) / kShortSlice;
@@ -378,7 +387,7 @@ __global__ void fill_items_kernel(const int *__restrict__ offsets, const int *__
         const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
         int4 it = make_int4(start[c] + k * kShortChunk, 0, 0, 0);
         it.y = min(kShortChunk, end[c] - it.x);
-        for (int r = 0; r < 9; ++r) {
+        for (int r = 0; r < kRows; ++r) {
             int j0, j1;
             if (!row_range(cx, cy, cz, r, nc, start, end, j0, j1)) continue;
             const int ns = (j1 - j0 + kShortSlice - 1) / kShortSlice;
@@ -641,9 +650,9 @@ cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t 
     m->L = L;
     m->x0 = c.lo - g * h;
     const double span = M * h;
-    m->nc = (int)std::floor(span / c.rc);
+    m->nc = (int)std::floor(span * kCellReach / c.rc);
     if (m->nc < 1) m->nc = 1;
-    if (m->nc > 256) m->nc = 256;
+    if (m->nc > 512) m->nc = 512;
     m->built = true;
     *what = "";
     return done(cudaSuccess);

@@ -177,55 +177,83 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     long long *iacc = reinterpret_cast<long long *>(smem + kSymHead + kSymStages * kSymStageBytes +
                                                     kSymJaccBytes);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t U = tri_count(a.tiles);
+    // Units: the tile pairs of one triangle, or of B triangles one after the
+    // other (batched: trajectory b owns units [unit0_b, unit0_{b+1})).
+    const int64_t U = a.traj ? a.units : tri_count(a.tiles);
     const int64_t u0 = U * blockIdx.x / a.ctas, u1 = U * (blockIdx.x + 1) / a.ctas;
     if (u0 >= u1) return;
+    auto tr_off = [&](int b) -> int64_t { return a.traj ? a.traj[b].off : 0; };
+    auto tr_n = [&](int b) -> int64_t { return a.traj ? a.traj[b].N : a.N; };
+    auto tr_tiles = [&](int b) -> int64_t { return a.traj ? a.traj[b].tiles : a.tiles; };
     if (tid == 0) {
         for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    const int nlast = (int)(a.N - (a.tiles - 1) * kTile);
-    auto count_of = [&](int64_t J) { return J == a.tiles - 1 ? nlast : kTile; };
-    auto advance = [&](int64_t &I, int64_t &J) {
-        if (++J == a.tiles) { ++I; J = I; }
+    auto count_of = [&](int b, int64_t J) {
+        const int64_t rem = tr_n(b) - J * kTile;
+        return rem < kTile ? (int)rem : kTile;
     };
-    auto issue = [&](uint32_t g, int64_t J) {
-        bulk_load(stage + (g % kSymStages) * kTile, a.pos + J * kTile,
-                  (uint32_t)(count_of(J) * sizeof(float4)), &bars[g % kSymStages]);
+    // next unit; past the last tile pair of trajectory b go to b + 1 (the
+    // prefetch cursor may run past the last unit: it then stops at b = B - 1)
+    auto advance = [&](int &b, int64_t &I, int64_t &J) {
+        if (++J == tr_tiles(b)) {
+            ++I;
+            J = I;
+            if (I == tr_tiles(b) && b + 1 < a.B) { ++b; I = 0; J = 0; }
+        }
+    };
+    auto issue = [&](uint32_t g, int b, int64_t J) {
+        bulk_load(stage + (g % kSymStages) * kTile, a.pos + tr_off(b) + J * kTile,
+                  (uint32_t)(count_of(b, J) * sizeof(float4)), &bars[g % kSymStages]);
     };
     const uint32_t n = (uint32_t)(u1 - u0);
+    int b = 0;
+    if (a.traj) {                        // trajectory of unit u0
+        int lo = 0, hi = a.B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.traj[mid].unit0 <= u0) lo = mid;
+            else hi = mid - 1;
+        }
+        b = lo;
+    }
     int64_t I, J, qI, qJ;
-    tri_pair(u0, a.tiles, I, J);
+    tri_pair(u0 - (a.traj ? a.traj[b].unit0 : 0), tr_tiles(b), I, J);
+    int qb = b;
     qI = I; qJ = J;                      // cursor of the next tile to prefetch
     for (uint32_t g = 0; g < n && g < (uint32_t)kSymStages; ++g) {
-        if (tid == 0) issue(g, qJ);
-        advance(qI, qJ);
+        if (tid == 0) issue(g, qb, qJ);
+        advance(qb, qI, qJ);
     }
+    int curB = -1;
     int64_t curI = -1;
     float tx[T], ty[T], tz[T], tm[T];
     // the thread's targets of tile curI: l = warp*128 + t*32 + lane
     auto flush_i = [&]() {
+        const int64_t nb = tr_n(curB), ob = tr_off(curB);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int64_t i = curI * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 long long &x = iacc[(t * NV + v) * kSymThreads + tid];
-                if (i < a.N) add_fix(&a.acc[i * NV + v], x);
+                if (i < nb) add_fix(&a.acc[(ob + i) * NV + v], x);
                 x = 0;
             }
         }
     };
     for (uint32_t g = 0; g < n; ++g) {
-        if (I != curI) {
+        if (I != curI || b != curB) {
             if (curI >= 0) flush_i();
             curI = I;
+            curB = b;
+            const int64_t nb = tr_n(b), ob = tr_off(b);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const int64_t i = I * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
-                const bool ok = i < a.N;
-                const float4 p = ok ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool ok = i < nb;
+                const float4 p = ok ? a.pos[ob + i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 tx[t] = p.x; ty[t] = p.y; tz[t] = p.z; tm[t] = ok ? 1.f : 0.f;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * kSymThreads + tid] = 0;
@@ -240,7 +268,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
             return;
         }
         const float4 *src = stage + (g % kSymStages) * kTile;
-        const int jvalid = count_of(J);
+        const int jvalid = count_of(b, J);
         float ai[T][3];
 #pragma unroll
         for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
@@ -256,7 +284,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
             for (int l = tid; l < jvalid; l += kSymThreads)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
-                    add_fix(&a.acc[(J * kTile + l) * NV + v], to_fix(jacc[v * kTile + l]));
+                    add_fix(&a.acc[(tr_off(b) + J * kTile + l) * NV + v], to_fix(jacc[v * kTile + l]));
         }
 #pragma unroll
         for (int t = 0; t < T; ++t)
@@ -266,11 +294,11 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
         if (g + kSymStages < n) {
             if (tid == 0) {
                 fence_proxy_async_smem();
-                issue(g + kSymStages, qJ);
+                issue(g + kSymStages, qb, qJ);
             }
-            advance(qI, qJ);
+            advance(qb, qI, qJ);
         }
-        advance(I, J);
+        advance(b, I, J);
     }
     flush_i();
 }

@@ -132,12 +132,14 @@ def test_mesh_repeatable_and_range_error(sp):
         ctx.close()
 
 
-@pytest.mark.parametrize("name,n_cells,m", [("diff", 128, 128), ("hr", 256, 64)])
-def test_mesh_full_size_sampled_targets(sp, name, n_cells, m):
-    """Full-size workloads with the mesh repulsion (sigma = 2.5 cells, rc = 4
+@pytest.mark.parametrize("name,n_cells,m,sc,rs", [("diff", 128, 128, 2.5, 4.0),
+                                                   ("hr", 256, 64, 2.5, 4.0),
+                                                   ("hr", 384, 64, 2.0, 3.5)])
+def test_mesh_full_size_sampled_targets(sp, name, n_cells, m, sc, rs):
+    """Full-size workloads with the mesh repulsion (sigma sc cells, rc = rs
     sigma): R and G on sampled targets against the oracle's direct sums."""
     p = inputs.make_problem(name)
-    ctx = mesh_ctx(sp, n_cells)
+    ctx = mesh_ctx(sp, n_cells, sc, rs)
     try:
         Kd = torch.from_numpy(p.K).cuda()
         rho = torch.from_numpy(p.grid.rho).cuda()
@@ -154,7 +156,8 @@ def test_mesh_full_size_sampled_targets(sp, name, n_cells, m):
     _, R0, G0 = oracle.forces(p.K.astype(np.float64), p.grid, targets=idx)
     eR = rel_l2(R.cpu().numpy()[idx], R0)
     eG = rel_l2(G.cpu().numpy()[idx], G0)
-    print(f"mesh repulsion {name} ({n_cells} cells): R rel L2 {eR:.2e}, G rel L2 {eG:.2e}, "
+    print(f"mesh repulsion {name} ({n_cells} cells, sigma {sc}, rc {rs}): R rel L2 {eR:.2e}, "
+          f"G rel L2 {eG:.2e}, "
           f"repulsion {t['repulsion'][0]:.1f} ms (first call, with the kernel spectra)")
     assert eR < 2e-5
     # the attraction here is the compensated-FP32 direct sum (about 1e-5 per
