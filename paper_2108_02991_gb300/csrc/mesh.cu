@@ -338,10 +338,9 @@ __device__ __forceinline__ bool row_range(int cx, int cy, int cz, int r, int nc,
     return j0 >= 0;
 }
 
-constexpr int kShortThreads = 128;
-constexpr int kShortChunk = 2 * kShortThreads;   // targets per item (2 per thread)
-constexpr int kShortSlice = 8192;                // sources per item at most
-constexpr int kShortTile = 1024;                 // sources per shared-memory tile
+constexpr int kShortThreads = 128;               // 4 warps, each takes its own items
+constexpr int kShortChunk = 64;                  // targets per item (2 per lane of a warp)
+constexpr int kShortSlice = 4096;                // sources per item at most
 
 // Items of cell c: ceil(n_c / kShortChunk) target chunks times the source
 // slices of its kRows rows.
@@ -428,10 +427,12 @@ __device__ __forceinline__ void short_pair(const float4 p, const float4 q, float
     }
 }
 
-// Persistent CTAs take items from a queue: kShortChunk targets of one cell
-// (two per thread) against up to kShortSlice sources of one neighbour row,
-// staged through shared memory in tiles; the item sums are added to the
-// targets' 64-bit fixed-point accumulators (exact, order-free).
+// Persistent warps take items from a queue: kShortChunk targets of one cell
+// (two per lane) against up to kShortSlice sources of one neighbour row.
+// The lanes of a warp read the same source at the same time (one broadcast
+// load serves 64 pairs); the item sums are added to the targets' 64-bit
+// fixed-point accumulators (exact, order-free).  Small items keep the lanes
+// busy where cells hold few samples.
 template <bool ENERGY>
 __global__ void __launch_bounds__(kShortThreads) short_items_kernel(
     const int4 *__restrict__ items, const int *__restrict__ n_items, unsigned int *queue,
@@ -439,40 +440,32 @@ __global__ void __launch_bounds__(kShortThreads) short_items_kernel(
     float spi, float eps2, unsigned long long *acc)
 {
     constexpr int NV = ENERGY ? 1 : 3;
-    __shared__ float4 src[kShortTile];
-    __shared__ int item_id;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int total = *n_items;
     for (;;) {
-        if (tid == 0) item_id = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int u = item_id;
-        __syncthreads();
+        int u = 0;
+        if (lane == 0) u = (int)atomicAdd(queue, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= total) break;
         const int4 it = items[u];
         float4 p[2];
         bool ok[2];
         float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         for (int t = 0; t < 2; ++t) {
-            const int l = tid + t * kShortThreads;
+            const int l = lane + 32 * t;
             ok[t] = l < it.y;
             p[t] = ok[t] ? spos[it.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int b = 0; b < it.w; b += kShortTile) {
-            const int cnt = min(kShortTile, it.w - b);
-            for (int e = tid; e < cnt; e += kShortThreads) src[e] = spos[it.z + b + e];
-            __syncthreads();
+        const float4 *src = spos + it.z;
 #pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
-                const float4 q = src[j];
-                short_pair<ENERGY>(p[0], q, rc2, inv_sigma, spi, eps2, f[0]);
-                short_pair<ENERGY>(p[1], q, rc2, inv_sigma, spi, eps2, f[1]);
-            }
-            __syncthreads();
+        for (int j = 0; j < it.w; ++j) {
+            const float4 q = __ldg(src + j);
+            short_pair<ENERGY>(p[0], q, rc2, inv_sigma, spi, eps2, f[0]);
+            short_pair<ENERGY>(p[1], q, rc2, inv_sigma, spi, eps2, f[1]);
         }
         for (int t = 0; t < 2; ++t) {
             if (!ok[t]) continue;
-            unsigned long long *a = acc + (int64_t)idx[it.x + tid + t * kShortThreads] * NV;
+            unsigned long long *a = acc + (int64_t)idx[it.x + lane + 32 * t] * NV;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const long long x = __float2ll_rn(f[t][v] * 4294967296.0f);
