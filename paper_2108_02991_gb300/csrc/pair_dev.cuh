@@ -105,10 +105,7 @@ __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const floa
                 for (int r = 0; r < NR; ++r) {
                     const float rho = j == 0 ? w[r].x : j == 1 ? w[r].y : j == 2 ? w[r].z : w[r].w;
                     const float r2 = fmaf(dx[j], dx[j], s2[r][t]);
-                    // one pair in 4 NR takes the FMA-pipe rsqrt: the SFU
-                    // (16 results per SM per clock) is the bound of this loop
-                    // and the FP32 pipe has issue slots to spare
-                    const float wt = rho * ((j == 3 && r == 0) ? rsqrt_fma(r2) : rsqrt_sfu(r2));
+                    const float wt = rho * rsqrt_sfu(r2);
                     if (ENERGY) {
                         sw[r][t] = fmaf(wt, r2, sw[r][t]);     // rho * |d|
                     } else {

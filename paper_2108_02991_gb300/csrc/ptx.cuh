@@ -85,22 +85,6 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
     return y;
 }
 
-// Reciprocal square root on the FP32 and integer pipes, for the share of the
-// pairs that an SFU-bound kernel moves off the SFU: the bit-level initial
-// estimate of the published fast inverse square root (C. Lomont, "Fast
-// inverse square root", 2003: constant 0x5f375a86) refined by three
-// Newton-Raphson steps y <- y (3/2 - (x/2) y^2): the relative error falls
-// from 1.8e-3 to 4.7e-6 to 3e-11 (then float rounding, a few ulp), as
-// accurate as the SFU's approximation, for normal x > 0.
-__device__ __forceinline__ float rsqrt_fma(float x)
-{
-    const float h = 0.5f * x;
-    float y = __int_as_float(0x5f375a86 - (__float_as_int(x) >> 1));
-    y = y * fmaf(-h * y, y, 1.5f);
-    y = y * fmaf(-h * y, y, 1.5f);
-    y = y * fmaf(-h * y, y, 1.5f);
-    return y;
-}
 
 // Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
