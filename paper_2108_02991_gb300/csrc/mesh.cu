@@ -56,16 +56,18 @@ __device__ double taper(double t)
     return a / (a + b);
 }
 
-// Component c (0..2 force, 3 potential) of the tapered long-range kernel
-// sampled at the offsets of the periodic 4M box (residue order).
-__global__ void fill_big_kernel(double *out, int Lb, double h, double sigma, double eps2,
-                                double r1, double r2, int c)
+// Component c (0..2 force, 3 potential) of the tapered long-range kernel at
+// the offsets of the periodic Lb = 4M box (residue order), planes z0 ..
+// z0 + nz - 1 of it: out[z - z0][y][x].
+__global__ void fill_slab_kernel(double *out, int Lb, int z0, int nz, double h, double sigma,
+                                 double eps2, double r1, double r2, int c)
 {
-    const int64_t total = (int64_t)Lb * Lb * Lb;
+    const int64_t total = (int64_t)nz * Lb * Lb;
     const double spi = sigma * 0.56418958354775628;   // sigma / sqrt(pi)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(e % Lb), iy = (int)((e / Lb) % Lb), iz = (int)(e / ((int64_t)Lb * Lb));
+        const int ix = (int)(e % Lb), iy = (int)((e / Lb) % Lb);
+        const int iz = z0 + (int)(e / ((int64_t)Lb * Lb));
         const double x = (ix <= Lb / 2 ? ix : ix - Lb) * h;
         const double y = (iy <= Lb / 2 ? iy : iy - Lb) * h;
         const double z = (iz <= Lb / 2 ? iz : iz - Lb) * h;
@@ -83,46 +85,73 @@ __global__ void fill_big_kernel(double *out, int Lb, double h, double sigma, dou
     }
 }
 
-// Division by the squared transform of the cubic B-spline window,
-// prod_a sinc(f_a)^8, f_a = frequency index / Lb in cycles per sample.
-__global__ void deconvolve_kernel(cufftDoubleComplex *k, int Lb)
+// One axis of the deconvolution: divide the spectrum of every 1-D line by
+// sinc(f)^8, the squared transform of the cubic B-spline window along that
+// axis (f = frequency index / Lb in cycles per sample).  Element e holds
+// frequency (e / inner) % nf.
+__global__ void deconvolve_axis_kernel(cufftDoubleComplex *k, int64_t n, int64_t inner, int nf,
+                                       int Lb)
 {
-    const int Lh = Lb / 2 + 1;
-    const int64_t total = (int64_t)Lb * Lb * Lh;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int fx = (int)(e % Lh), fy = (int)((e / Lh) % Lb), fz = (int)(e / ((int64_t)Lh * Lb));
-        const int f[3] = {fx, fy <= Lb / 2 ? fy : fy - Lb, fz <= Lb / 2 ? fz : fz - Lb};
-        double w = 1.0;
-        for (int a = 0; a < 3; ++a) {
-            if (f[a] != 0) {
-                const double t = 3.14159265358979323846 * f[a] / Lb;
-                const double s = sin(t) / t;
-                const double s2 = s * s, s4 = s2 * s2;
-                w *= s4 * s4;
-            }
-        }
+        const int f = (int)((e / inner) % nf);
+        if (f == 0) continue;
+        const double t = 3.14159265358979323846 * f / Lb;
+        const double s = sin(t) / t, s2 = s * s, s4 = s2 * s2;
+        const double w = s4 * s4;
         k[e].x /= w;
         k[e].y /= w;
     }
 }
 
-// The deconvolved kernel at the offsets |m_a| < M of the 4M box, placed in
-// the L = 2M box (residue order, offset M unused), scaled by `scale`.
-__global__ void extract_small_kernel(float *out, const double *big, int Lb, int L, int M,
-                                     double scale)
+// Offset index of the L = 2M box (residue order; index M unused) -> index
+// of the Lb box, or -1 for the unused index.
+__device__ __forceinline__ int small_to_big(int i, int M, int Lb)
 {
-    const int64_t total = (int64_t)L * L * L;
+    if (i == M) return -1;
+    const int m = i < M ? i : i - 2 * M;
+    return (m + Lb) % Lb;
+}
+
+// Pass 1 (x): src[zz][y][x] (x over Lb) -> a1[z0 + zz][y][xs] (xs over 2M).
+__global__ void keep_x_kernel(double *a1, const double *src, int z0, int nz, int Lb, int M)
+{
+    const int L = 2 * M;
+    const int64_t total = (int64_t)nz * Lb * L;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(e % L), iy = (int)((e / L) % L), iz = (int)(e / ((int64_t)L * L));
-        if (ix == M || iy == M || iz == M) {
-            out[e] = 0.f;
-            continue;
-        }
-        const int mx = ix < M ? ix : ix - L, my = iy < M ? iy : iy - L, mz = iz < M ? iz : iz - L;
-        const int bx = (mx + Lb) % Lb, by = (my + Lb) % Lb, bz = (mz + Lb) % Lb;
-        out[e] = (float)(big[((int64_t)bz * Lb + by) * Lb + bx] * scale);
+        const int xs = (int)(e % L);
+        const int64_t row = e / L;                       // zz * Lb + y
+        const int bx = small_to_big(xs, M, Lb);
+        a1[((int64_t)z0 * Lb) * L + e] = bx < 0 ? 0.0 : src[row * Lb + bx];
+    }
+}
+
+// Pass 2 (y): plane src[y][x] (y over Lb, x over 2M) -> a2[z][ys][x].
+__global__ void keep_y_kernel(double *a2, const double *src, int z, int Lb, int M)
+{
+    const int L = 2 * M;
+    const int64_t total = (int64_t)L * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e % L), ys = (int)(e / L);
+        const int by = small_to_big(ys, M, Lb);
+        a2[(int64_t)z * L * L + e] = by < 0 ? 0.0 : src[(int64_t)by * L + x];
+    }
+}
+
+// Pass 3 (z): plane src[z][x] (z over Lb, x over 2M) for row ys -> the
+// float L box out[zs][ys][x], scaled.
+__global__ void keep_z_kernel(float *out, const double *src, int ys, int Lb, int M, double scale)
+{
+    const int L = 2 * M;
+    const int64_t total = (int64_t)L * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e % L), zs = (int)(e / L);
+        const int bz = small_to_big(zs, M, Lb);
+        out[((int64_t)zs * L + ys) * L + x] =
+            bz < 0 ? 0.f : (float)(src[(int64_t)bz * L + x] * scale);
     }
 }
 
@@ -310,7 +339,7 @@ __device__ __forceinline__ float erfc_as(float x, float &gauss)
 // Cells have side >= rc / kCellReach, so the pairs closer than rc lie in the
 // (2 kCellReach + 1)^3 cells around a sample's cell (smaller cells: fewer
 // candidate pairs beyond rc).
-constexpr int kCellReach = 2;
+constexpr int kCellReach = 3;
 constexpr int kRowSpan = 2 * kCellReach + 1;
 constexpr int kRows = kRowSpan * kRowSpan;
 
@@ -561,66 +590,110 @@ cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t 
 {
     m->built = false;
     const int g = mesh_guard(c.n_cells);
-    const int M = c.n_cells + 2 * g, L = 2 * M, Lb = 4 * M;
+    const int M = c.n_cells + 2 * g, L = 2 * M, Lb = 4 * M, nf = Lb / 2 + 1;
     const double h = (c.hi - c.lo) / c.n_cells;
-    const int64_t nb = (int64_t)Lb * Lb * Lb, nbc = (int64_t)Lb * Lb * (Lb / 2 + 1);
     const int64_t nl = (int64_t)L * L * L, nlc = (int64_t)L * L * (L / 2 + 1);
-    double *big = nullptr;
-    cufftDoubleComplex *bigc = nullptr;
+    // The deconvolution divides by a product of one factor per axis, so it
+    // runs as three passes of 1-D transforms over the Lb = 4M box, each
+    // keeping only the offsets |m| < M of its axis: pass 1 (x) on slabs of
+    // kSlab planes of the kernel generated on the fly, pass 2 (y) per z
+    // plane, pass 3 (z) per y row.  Peak memory: a1 = Lb * Lb * 2M and
+    // a2 = Lb * 2M * 2M doubles (the full box would be Lb^3).
+    constexpr int kSlab = 8;
+    double *a1 = nullptr, *a2 = nullptr, *rbuf = nullptr;
+    cufftDoubleComplex *cbuf = nullptr;
     float *small = nullptr;
     void *work = nullptr;
-    cufftHandle fwd = 0, inv = 0, sfwd = 0;
-    bool hf = false, hi = false, hs = false;
+    cufftHandle px_f = 0, px_i = 0, py_f = 0, py_i = 0, pz_f = 0, pz_i = 0, sfwd = 0;
+    bool made[7] = {false, false, false, false, false, false, false};
+    cufftHandle *handles[7] = {&px_f, &px_i, &py_f, &py_i, &pz_f, &pz_i, &sfwd};
     cudaError_t err = cudaSuccess;
     auto done = [&](cudaError_t e) {
-        if (hf) cufftDestroy(fwd);
-        if (hi) cufftDestroy(inv);
-        if (hs) cufftDestroy(sfwd);
-        cudaFree(big);
-        cudaFree(bigc);
-        cudaFree(small);
+        for (int k = 0; k < 7; ++k)
+            if (made[k]) cufftDestroy(*handles[k]);
+        cudaFree(a1); cudaFree(a2); cudaFree(rbuf); cudaFree(cbuf); cudaFree(small);
         cudaFree(work);
         return e;
     };
-    // the three plans run one after another: one shared work area
-    auto plan = [](cufftHandle *p, int n, cufftType t, size_t *ws, bool &made) {
-        if (cufftCreate(p) != CUFFT_SUCCESS) return false;
-        made = true;
-        return cufftSetAutoAllocation(*p, 0) == CUFFT_SUCCESS &&
-               cufftMakePlan3d(*p, n, n, n, t, ws) == CUFFT_SUCCESS;
-    };
     *what = "mesh kernel buffers";
-    if ((err = grow(m->spectra, m->spectra_cap, (size_t)4 * nlc * sizeof(cufftComplex))) != cudaSuccess)
+    const size_t rbuf_n = std::max((size_t)kSlab * Lb * Lb, (size_t)Lb * L);
+    const size_t cbuf_n = std::max((size_t)kSlab * Lb * nf, (size_t)nf * L);
+    if ((err = grow(m->spectra, m->spectra_cap, (size_t)4 * nlc * sizeof(cufftComplex))) ||
+        (err = cudaMalloc(&a1, (size_t)Lb * Lb * L * sizeof(double))) ||
+        (err = cudaMalloc(&a2, (size_t)Lb * L * L * sizeof(double))) ||
+        (err = cudaMalloc(&rbuf, rbuf_n * sizeof(double))) ||
+        (err = cudaMalloc(&cbuf, cbuf_n * sizeof(cufftDoubleComplex))) ||
+        (err = cudaMalloc(&small, nl * sizeof(float))))
         return done(err);
-    if ((err = cudaMalloc(&big, nb * sizeof(double))) != cudaSuccess) return done(err);
-    if ((err = cudaMalloc(&bigc, nbc * sizeof(cufftDoubleComplex))) != cudaSuccess) return done(err);
-    if ((err = cudaMalloc(&small, nl * sizeof(float))) != cudaSuccess) return done(err);
     *what = "mesh cuFFT plans";
-    size_t w1 = 0, w2 = 0, w3 = 0;
-    if (!plan(&fwd, Lb, CUFFT_D2Z, &w1, hf) || !plan(&inv, Lb, CUFFT_Z2D, &w2, hi) ||
-        !plan(&sfwd, L, CUFFT_R2C, &w3, hs))
+    // 1-D plans: n = Lb; x: contiguous lines; y, z: lines of stride L (x the batch)
+    int n1[1] = {Lb}, nfe[1] = {nf};
+    size_t ws[7] = {0, 0, 0, 0, 0, 0, 0};
+    auto many = [&](int k, int istride, int idist, int ostride, int odist, int batch, cufftType t,
+                    bool real_in) {
+        if (cufftCreate(handles[k]) != CUFFT_SUCCESS) return false;
+        made[k] = true;
+        int *inem = real_in ? n1 : nfe, *onem = real_in ? nfe : n1;
+        return cufftSetAutoAllocation(*handles[k], 0) == CUFFT_SUCCESS &&
+               cufftMakePlanMany(*handles[k], 1, n1, inem, istride, idist, onem, ostride, odist,
+                                 t, batch, &ws[k]) == CUFFT_SUCCESS;
+    };
+    if (!many(0, 1, Lb, 1, nf, kSlab * Lb, CUFFT_D2Z, true) ||
+        !many(1, 1, nf, 1, Lb, kSlab * Lb, CUFFT_Z2D, false) ||
+        !many(2, L, 1, L, 1, L, CUFFT_D2Z, true) || !many(3, L, 1, L, 1, L, CUFFT_Z2D, false) ||
+        !many(4, L * L, 1, L, 1, L, CUFFT_D2Z, true) || !many(5, L, 1, L, 1, L, CUFFT_Z2D, false))
+        return done(cudaErrorUnknown);
+    if (cufftCreate(&sfwd) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+    made[6] = true;
+    if (cufftSetAutoAllocation(sfwd, 0) != CUFFT_SUCCESS ||
+        cufftMakePlan3d(sfwd, L, L, L, CUFFT_R2C, &ws[6]) != CUFFT_SUCCESS)
         return done(cudaErrorUnknown);
     *what = "mesh cuFFT work area";
-    if ((err = cudaMalloc(&work, std::max(std::max(w1, w2), std::max(w3, (size_t)256)))) != cudaSuccess)
-        return done(err);
-    if (cufftSetWorkArea(fwd, work) != CUFFT_SUCCESS || cufftSetWorkArea(inv, work) != CUFFT_SUCCESS ||
-        cufftSetWorkArea(sfwd, work) != CUFFT_SUCCESS || cufftSetStream(fwd, st) != CUFFT_SUCCESS ||
-        cufftSetStream(inv, st) != CUFFT_SUCCESS || cufftSetStream(sfwd, st) != CUFFT_SUCCESS)
-        return done(cudaErrorUnknown);
+    size_t wmax = 256;
+    for (int k = 0; k < 7; ++k) wmax = std::max(wmax, ws[k]);
+    if ((err = cudaMalloc(&work, wmax))) return done(err);
+    for (int k = 0; k < 7; ++k)
+        if (cufftSetWorkArea(*handles[k], work) != CUFFT_SUCCESS ||
+            cufftSetStream(*handles[k], st) != CUFFT_SUCCESS)
+            return done(cudaErrorUnknown);
     *what = "mesh kernel spectra";
     const double r1 = std::sqrt(3.0) * M * h, r2 = 2.0 * M * h;
-    const double scale = 1.0 / ((double)nb * (double)nl);
+    const double scale = 1.0 / ((double)Lb * Lb * Lb * (double)nl);
     for (int comp = 0; comp < 4; ++comp) {
-        fill_big_kernel<<<grid_for(nb, sms), kMeshThreads, 0, st>>>(big, Lb, h, c.sigma,
-                                                                   c.eps * c.eps, r1, r2, comp);
-        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
-        if (cufftExecD2Z(fwd, big, bigc) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
-        deconvolve_kernel<<<grid_for(nbc, sms), kMeshThreads, 0, st>>>(bigc, Lb);
-        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
-        if (cufftExecZ2D(inv, bigc, big) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
-        extract_small_kernel<<<grid_for(nl, sms), kMeshThreads, 0, st>>>(small, big, Lb, L, M,
-                                                                        scale);
-        if ((err = cudaGetLastError()) != cudaSuccess) return done(err);
+        // pass 1: x lines of up to kSlab planes at a time (the plan always
+        // transforms kSlab planes; rows past the last plane are not kept)
+        for (int z0 = 0; z0 < Lb; z0 += kSlab) {
+            const int nzz = std::min(kSlab, Lb - z0);
+            const int64_t nr = (int64_t)nzz * Lb * Lb;
+            fill_slab_kernel<<<grid_for(nr, sms), kMeshThreads, 0, st>>>(
+                rbuf, Lb, z0, nzz, h, c.sigma, c.eps * c.eps, r1, r2, comp);
+            if (cufftExecD2Z(px_f, rbuf, cbuf) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+            deconvolve_axis_kernel<<<grid_for((int64_t)kSlab * Lb * nf, sms), kMeshThreads, 0, st>>>(
+                cbuf, (int64_t)kSlab * Lb * nf, 1, nf, Lb);
+            if (cufftExecZ2D(px_i, cbuf, rbuf) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+            keep_x_kernel<<<grid_for((int64_t)nzz * Lb * L, sms), kMeshThreads, 0, st>>>(
+                a1, rbuf, z0, nzz, Lb, M);
+        }
+        // pass 2: y lines of every z plane of a1
+        for (int z = 0; z < Lb; ++z) {
+            if (cufftExecD2Z(py_f, a1 + (int64_t)z * Lb * L, cbuf) != CUFFT_SUCCESS)
+                return done(cudaErrorUnknown);
+            deconvolve_axis_kernel<<<grid_for((int64_t)nf * L, sms), kMeshThreads, 0, st>>>(
+                cbuf, (int64_t)nf * L, L, nf, Lb);
+            if (cufftExecZ2D(py_i, cbuf, rbuf) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+            keep_y_kernel<<<grid_for((int64_t)L * L, sms), kMeshThreads, 0, st>>>(a2, rbuf, z, Lb, M);
+        }
+        // pass 3: z lines of every y row of a2, into the float L box
+        for (int ys = 0; ys < L; ++ys) {
+            if (cufftExecD2Z(pz_f, a2 + (int64_t)ys * L, cbuf) != CUFFT_SUCCESS)
+                return done(cudaErrorUnknown);
+            deconvolve_axis_kernel<<<grid_for((int64_t)nf * L, sms), kMeshThreads, 0, st>>>(
+                cbuf, (int64_t)nf * L, L, nf, Lb);
+            if (cufftExecZ2D(pz_i, cbuf, rbuf) != CUFFT_SUCCESS) return done(cudaErrorUnknown);
+            keep_z_kernel<<<grid_for((int64_t)L * L, sms), kMeshThreads, 0, st>>>(small, rbuf, ys, Lb,
+                                                                                  M, scale);
+        }
+        if ((err = cudaGetLastError())) return done(err);
         if (cufftExecR2C(sfwd, small, m->spectra + comp * nlc) != CUFFT_SUCCESS)
             return done(cudaErrorUnknown);
     }

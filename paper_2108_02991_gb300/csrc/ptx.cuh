@@ -85,7 +85,6 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
     return y;
 }
 
-
 // Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
