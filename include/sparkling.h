@@ -365,9 +365,10 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
  *     kernel, interpolation back); the energy the same way with the matching
  *     potential.  Approximate: its error against the direct sum is measured
  *     by the caller.  The kernel spectra are built at the first call that
- *     needs them (blocking, about 100 L^3 bytes of temporary device memory,
- *     L = 4 (n_cells + 2g)), again when the mesh or the regularisation
- *     changes.  A sample outside the mesh gives SPARKLING_E_RANGE.  Each
+ *     needs them (blocking; about 384 M^3 bytes of temporary device memory,
+ *     M = n_cells + 2g), again when the mesh or the regularisation changes;
+ *     the context then keeps about 330 M^3 bytes (spectra, FFT and charge
+ *     buffers) plus 80 bytes per sample.  A sample outside the mesh gives SPARKLING_E_RANGE.  Each
  *     evaluation reads the size of its short-range work list back to the
  *     host (one stream synchronisation), so it cannot be stream-captured.
  * Returns SPARKLING_E_INVAL for a bad mode or mesh. */
