@@ -61,11 +61,11 @@ def parse_args(argv=None):
     ap.add_argument("--repulsion", choices=("direct", "mesh"), default="direct",
                     help="every pair (exact) or the particle-particle particle-mesh summation "
                          "(fast, approximate; pairs counted as equivalent pair interactions)")
-    ap.add_argument("--mesh-cells", type=int, default=256,
+    ap.add_argument("--mesh-cells", type=int, default=512,
                     help="mesh cells across the sample box for --repulsion mesh")
-    ap.add_argument("--mesh-sigma", type=float, default=2.5,
+    ap.add_argument("--mesh-sigma", type=float, default=2.0,
                     help="split width in mesh cells for --repulsion mesh")
-    ap.add_argument("--mesh-rc", type=float, default=4.0,
+    ap.add_argument("--mesh-rc", type=float, default=3.5,
                     help="short-range cut-off in split widths for --repulsion mesh")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

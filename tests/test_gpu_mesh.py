@@ -134,7 +134,8 @@ def test_mesh_repeatable_and_range_error(sp):
 
 @pytest.mark.parametrize("name,n_cells,m,sc,rs", [("diff", 128, 128, 2.5, 4.0),
                                                    ("hr", 256, 64, 2.5, 4.0),
-                                                   ("hr", 384, 64, 2.0, 3.5)])
+                                                   ("hr", 384, 64, 2.0, 3.5),
+                                                   ("hr", 512, 64, 2.0, 3.5)])
 def test_mesh_full_size_sampled_targets(sp, name, n_cells, m, sc, rs):
     """Full-size workloads with the mesh repulsion (sigma sc cells, rc = rs
     sigma): R and G on sampled targets against the oracle's direct sums."""
