@@ -30,6 +30,7 @@ import statistics
 import subprocess
 import sys
 import time
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -67,6 +68,8 @@ def parse_args(argv=None):
                     help="split width in mesh cells for --repulsion mesh")
     ap.add_argument("--mesh-rc", type=float, default=3.5,
                     help="short-range cut-off in split widths for --repulsion mesh")
+    ap.add_argument("--clock-log", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: the temp dir)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -134,10 +137,11 @@ def pairs_per_step(N: int, P: int) -> int:
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, directory: Optional[str] = None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -360,7 +364,7 @@ def run_ours(args):
     sp.sparkling_set_timing(ctx, True)
     sp.sparkling_kernel_times(ctx, reset=True)
     launches0 = sp.sparkling_launch_count(ctx)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clock_log)
     clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
