@@ -165,9 +165,12 @@ __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const f
 
 constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 
-template <bool ENERGY, int S>
+// REG: the regularisation eps^2 is a kernel argument; without it the
+// zero-distance guard kEps2 is a compile-time constant of the pair loop.
+template <bool ENERGY, int S, bool REG>
 __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
 {
+    const float eps2 = REG ? a.eps2 : kEps2;
     constexpr int T = kSymT;
     constexpr int NV = ENERGY ? 1 : 3;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -273,14 +276,14 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
 #pragma unroll
         for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
         if (I == J) {
-            diag_item<ENERGY>(src, jvalid, tx, ty, tz, a.eps2, ai);
+            diag_item<ENERGY>(src, jvalid, tx, ty, tz, eps2, ai);
         } else {
             for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
             __syncthreads();
             if (jvalid < kTile)
-                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, a.eps2, ai, jacc);
+                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
             else
-                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, a.eps2, ai, jacc);
+                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
             for (int l = tid; l < jvalid; l += kSymThreads)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -303,11 +306,17 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     flush_i();
 }
 
-template <bool E>
-void *sym_fn(int variant)
+template <bool E, bool REG>
+void *sym_fn_reg(int variant)
 {
-    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4>)
-                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2>);
+    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG>)
+                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG>);
+}
+
+template <bool E>
+void *sym_fn(int variant, bool reg = true)
+{
+    return reg ? sym_fn_reg<E, true>(variant) : sym_fn_reg<E, false>(variant);
 }
 
 } // namespace
@@ -321,19 +330,27 @@ size_t repulsion_sym_smem_bytes()
 
 int repulsion_sym_ctas_per_sm(bool energy, int variant)
 {
-    void *fn = energy ? sym_fn<true>(variant) : sym_fn<false>(variant);
-    const size_t smem = repulsion_sym_smem_bytes();
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kSymThreads, smem) != cudaSuccess)
-        return 0;
-    return n;
+    // both instances (eps^2 argument or constant) take the same resources
+    // here; the smaller occupancy of the two sizes the grid
+    int best = 1 << 30;
+    for (int reg = 0; reg < 2; ++reg) {
+        void *fn = energy ? sym_fn<true>(variant, reg != 0) : sym_fn<false>(variant, reg != 0);
+        const size_t smem = repulsion_sym_smem_bytes();
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kSymThreads, smem) != cudaSuccess)
+            return 0;
+        best = n < best ? n : best;
+    }
+    return best;
 }
 
 cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st)
 {
-    void *fn = energy ? sym_fn<true>(variant) : sym_fn<false>(variant);
+    const bool reg = a.eps2 > kEps2;
+    void *fn = energy ? sym_fn<true>(variant, reg) : sym_fn<false>(variant, reg);
     void *args[] = {const_cast<SymArgs *>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(kSymThreads), args,
                             repulsion_sym_smem_bytes(), st);
