@@ -167,7 +167,8 @@ constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 
 // REG: the regularisation eps^2 is a kernel argument; without it the
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
-template <bool ENERGY, int S, bool REG>
+// BATCHED: the units of a.B trajectories (a.traj), else of one.
+template <bool ENERGY, int S, bool REG, bool BATCHED>
 __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
@@ -182,12 +183,12 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // Units: the tile pairs of one triangle, or of B triangles one after the
     // other (batched: trajectory b owns units [unit0_b, unit0_{b+1})).
-    const int64_t U = a.traj ? a.units : tri_count(a.tiles);
+    const int64_t U = BATCHED ? a.units : tri_count(a.tiles);
     const int64_t u0 = U * blockIdx.x / a.ctas, u1 = U * (blockIdx.x + 1) / a.ctas;
     if (u0 >= u1) return;
-    auto tr_off = [&](int b) -> int64_t { return a.traj ? a.traj[b].off : 0; };
-    auto tr_n = [&](int b) -> int64_t { return a.traj ? a.traj[b].N : a.N; };
-    auto tr_tiles = [&](int b) -> int64_t { return a.traj ? a.traj[b].tiles : a.tiles; };
+    auto tr_off = [&](int b) -> int64_t { return BATCHED ? a.traj[b].off : 0; };
+    auto tr_n = [&](int b) -> int64_t { return BATCHED ? a.traj[b].N : a.N; };
+    auto tr_tiles = [&](int b) -> int64_t { return BATCHED ? a.traj[b].tiles : a.tiles; };
     if (tid == 0) {
         for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
         if (++J == tr_tiles(b)) {
             ++I;
             J = I;
-            if (I == tr_tiles(b) && b + 1 < a.B) { ++b; I = 0; J = 0; }
+            if (BATCHED && I == tr_tiles(b) && b + 1 < a.B) { ++b; I = 0; J = 0; }
         }
     };
     auto issue = [&](uint32_t g, int b, int64_t J) {
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     };
     const uint32_t n = (uint32_t)(u1 - u0);
     int b = 0;
-    if (a.traj) {                        // trajectory of unit u0
+    if (BATCHED) {                       // trajectory of unit u0
         int lo = 0, hi = a.B - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
         b = lo;
     }
     int64_t I, J, qI, qJ;
-    tri_pair(u0 - (a.traj ? a.traj[b].unit0 : 0), tr_tiles(b), I, J);
+    tri_pair(u0 - (BATCHED ? a.traj[b].unit0 : 0), tr_tiles(b), I, J);
     int qb = b;
     qI = I; qJ = J;                      // cursor of the next tile to prefetch
     for (uint32_t g = 0; g < n && g < (uint32_t)kSymStages; ++g) {
@@ -306,17 +307,18 @@ __global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const Sym
     flush_i();
 }
 
-template <bool E, bool REG>
+template <bool E, bool REG, bool BATCHED>
 void *sym_fn_reg(int variant)
 {
-    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG>)
-                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG>);
+    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG, BATCHED>)
+                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG, BATCHED>);
 }
 
 template <bool E>
-void *sym_fn(int variant, bool reg = true)
+void *sym_fn(int variant, bool reg = true, bool batched = false)
 {
-    return reg ? sym_fn_reg<E, true>(variant) : sym_fn_reg<E, false>(variant);
+    if (batched) return reg ? sym_fn_reg<E, true, true>(variant) : sym_fn_reg<E, false, true>(variant);
+    return reg ? sym_fn_reg<E, true, false>(variant) : sym_fn_reg<E, false, false>(variant);
 }
 
 } // namespace
@@ -330,11 +332,12 @@ size_t repulsion_sym_smem_bytes()
 
 int repulsion_sym_ctas_per_sm(bool energy, int variant)
 {
-    // both instances (eps^2 argument or constant) take the same resources
-    // here; the smaller occupancy of the two sizes the grid
+    // the instances (eps^2 argument or constant, one trajectory or a batch)
+    // take about the same resources; the smallest occupancy sizes the grid
     int best = 1 << 30;
-    for (int reg = 0; reg < 2; ++reg) {
-        void *fn = energy ? sym_fn<true>(variant, reg != 0) : sym_fn<false>(variant, reg != 0);
+    for (int k = 0; k < 4; ++k) {
+        const bool reg = (k & 1) != 0, batched = (k & 2) != 0;
+        void *fn = energy ? sym_fn<true>(variant, reg, batched) : sym_fn<false>(variant, reg, batched);
         const size_t smem = repulsion_sym_smem_bytes();
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -349,8 +352,8 @@ int repulsion_sym_ctas_per_sm(bool energy, int variant)
 
 cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st)
 {
-    const bool reg = a.eps2 > kEps2;
-    void *fn = energy ? sym_fn<true>(variant, reg) : sym_fn<false>(variant, reg);
+    const bool reg = a.eps2 > kEps2, batched = a.traj != nullptr;
+    void *fn = energy ? sym_fn<true>(variant, reg, batched) : sym_fn<false>(variant, reg, batched);
     void *args[] = {const_cast<SymArgs *>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(kSymThreads), args,
                             repulsion_sym_smem_bytes(), st);
