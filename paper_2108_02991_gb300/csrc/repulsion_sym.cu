@@ -64,10 +64,22 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
                                          float eps2, float (*ai)[3], float *jacc)
 {
     constexpr int T = kSymT;
+    constexpr int P = T / 2;                    // target pairs (paired FP32 lanes)
     constexpr int kSymChunk = 32 * S, kChunks = kTile / kSymChunk;
     static_assert(kChunks >= kSymWarps && (kChunks & (kChunks - 1)) == 0, "chunk count");
+    static_assert(T % 2 == 0, "targets are processed in pairs");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int from = (lane + 1) & 31;
+    // targets (2p, 2p+1) and their sums in the two halves of 64-bit registers
+    f2 TX[P], TY[P], TZ[P], AX[P], AY[P], AZ[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        TX[p] = f2_pack(tx[2 * p], tx[2 * p + 1]);
+        TY[p] = f2_pack(ty[2 * p], ty[2 * p + 1]);
+        TZ[p] = f2_pack(tz[2 * p], tz[2 * p + 1]);
+        AX[p] = AY[p] = AZ[p] = f2_pack(0.f, 0.f);
+    }
+    const f2 E2 = f2_pack(eps2, eps2);
     for (int r = 0; r < kChunks; ++r) {
         const int c = (warp + r) & (kChunks - 1);
         float sx[S], sy[S], sz[S], sm[S], bx[S], by[S], bz[S];
@@ -84,25 +96,43 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
         }
         for (int step = 0; step < 32; ++step) {
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
+            for (int s = 0; s < S; ++s) {
+                const f2 SX = f2_pack(sx[s], sx[s]), SY = f2_pack(sy[s], sy[s]),
+                         SZ = f2_pack(sz[s], sz[s]);
+                f2 QX, QY, QZ;                  // the source's share, summed over the pairs
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const float dx = tx[t] - sx[s], dy = ty[t] - sy[s], dz = tz[t] - sz[s];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                    float ri = rsqrt_sfu(r2);
-                    if (RAGGED) ri *= tm[t] * sm[s];
+                for (int p = 0; p < P; ++p) {
+                    const f2 DX = f2_sub(TX[p], SX), DY = f2_sub(TY[p], SY),
+                             DZ = f2_sub(TZ[p], SZ);
+                    const f2 R2 = f2_fma(DX, DX, f2_fma(DY, DY, f2_fma(DZ, DZ, E2)));
+                    float r2a, r2b;
+                    f2_unpack(R2, r2a, r2b);
+                    f2 RI = f2_pack(rsqrt_sfu(r2a), rsqrt_sfu(r2b));
+                    if (RAGGED) RI = f2_mul(RI, f2_pack(tm[2 * p] * sm[s], tm[2 * p + 1] * sm[s]));
                     if (ENERGY) {
-                        const float e = r2 * ri;          // |d|, counted for both samples
-                        ai[t][0] += e;
-                        bx[s] += e;
+                        const f2 E = f2_mul(R2, RI);     // |d|, counted for both samples
+                        AX[p] = f2_add(AX[p], E);
+                        QX = p == 0 ? E : f2_add(QX, E);
                     } else {
-                        ai[t][0] = fmaf(dx, ri, ai[t][0]);
-                        ai[t][1] = fmaf(dy, ri, ai[t][1]);
-                        ai[t][2] = fmaf(dz, ri, ai[t][2]);
-                        bx[s] = fmaf(-dx, ri, bx[s]);
-                        by[s] = fmaf(-dy, ri, by[s]);
-                        bz[s] = fmaf(-dz, ri, bz[s]);
+                        AX[p] = f2_fma(DX, RI, AX[p]);
+                        AY[p] = f2_fma(DY, RI, AY[p]);
+                        AZ[p] = f2_fma(DZ, RI, AZ[p]);
+                        QX = p == 0 ? f2_mul(DX, RI) : f2_fma(DX, RI, QX);
+                        QY = p == 0 ? f2_mul(DY, RI) : f2_fma(DY, RI, QY);
+                        QZ = p == 0 ? f2_mul(DZ, RI) : f2_fma(DZ, RI, QZ);
                     }
+                }
+                float u, v;
+                if (ENERGY) {
+                    f2_unpack(QX, u, v);
+                    bx[s] += u + v;
+                } else {                        // the pair term is odd: the source gets -term
+                    f2_unpack(QX, u, v);
+                    bx[s] -= u + v;
+                    f2_unpack(QY, u, v);
+                    by[s] -= u + v;
+                    f2_unpack(QZ, u, v);
+                    bz[s] -= u + v;
                 }
             }
             // the sources and their sums move one lane down
@@ -131,6 +161,21 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
             }
         }
         __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        float u, v;
+        f2_unpack(AX[p], u, v);
+        ai[2 * p][0] += u;
+        ai[2 * p + 1][0] += v;
+        if (!ENERGY) {
+            f2_unpack(AY[p], u, v);
+            ai[2 * p][1] += u;
+            ai[2 * p + 1][1] += v;
+            f2_unpack(AZ[p], u, v);
+            ai[2 * p][2] += u;
+            ai[2 * p + 1][2] += v;
+        }
     }
 }
 
@@ -169,7 +214,7 @@ constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
 // BATCHED: the units of a.B trajectories (a.traj), else of one.
 template <bool ENERGY, int S, bool REG, bool BATCHED>
-__global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
+__global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
     constexpr int T = kSymT;
