@@ -104,6 +104,8 @@ def test_argument_validation_before_any_cuda_call(lib):
         "grid is NULL": grad(grid=None),
         "G is NULL": grad(G=None),
         "G dtype": grad(gd=2),
+        "N beyond the 32-bit sample index": grad(N=(1 << 31)),
+        "N far beyond": grad(N=(1 << 40)),
     }
     bad = lib.Grid(); bad.rho, bad.lo, bad.hi = dummy, 0.5, -0.5
     for a in range(3):
@@ -117,6 +119,11 @@ def test_argument_validation_before_any_cuda_call(lib):
     cases["n[1]"] = grad(grid=bad3)
     for what, code in cases.items():
         assert code == lib.E_INVAL, what
+    # shot shapes at and beyond the limits
+    assert L.sparkling_step(h, dummy, 0, 4, 65537, ctypes.byref(g), 0, 1e-3, ctypes.byref(p),
+                            None) == lib.E_INVAL          # Ns > 65536
+    assert L.sparkling_step(h, dummy, 0, (1 << 40), 8, ctypes.byref(g), 0, 1e-3, ctypes.byref(p),
+                            None) == lib.E_INVAL          # Nc * Ns too large
     # projection parameters
     def proj(Nc=4, Ns=8, pr=p):
         return L.sparkling_project(h, dummy, 0, Nc, Ns, ctypes.byref(pr) if pr else None, None, None)

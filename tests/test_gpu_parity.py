@@ -89,6 +89,18 @@ def test_grad_ragged_shapes(sp, ctx, N, shape, lo, hi, dt):
         assert_grad_close(G, G0, "G")
 
 
+def test_grad_longest_grid_rows(sp, ctx):
+    """Grid rows of the largest supported length (nx = 4096: one row fills a
+    pipeline stage) and a ragged target tail."""
+    rng = np.random.default_rng(71)
+    K = rng.uniform(-0.5, 0.5, size=(1500, 3)).astype(np.float32)
+    grid = random_grid(4096, 3, 2, seed=72)
+    A0, R0, G0 = oracle.forces(K, grid)
+    G, A, R = gpu_grad(sp, ctx, K, grid)
+    assert_grad_close(A, A0, "A")
+    assert_grad_close(G, G0, "G")
+
+
 def test_grad_many_source_blocks_and_tiles(sp, ctx):
     """N = 9000: 9 tiles, 9 repulsion source blocks (the last ragged), spokes."""
     K = inputs.radial_spokes(18, 500, 0.23, jitter=1e-3, seed=3, dtype=np.float32)
@@ -177,6 +189,8 @@ def test_project_tiny_fixed_iterations(sp, ctx):
     (9, 512, np.float32, dict(pin_index=256)),                          # f32, one sample/thread
     (3, 1500, np.float64, dict()),                                      # > 1024 samples per shot
     (3, 2560, np.float32, dict(pin_index=1280)),                        # state in global memory
+    (2, 65536, np.float64, dict(pin_index=32768)),                      # the largest Ns
+    (2, 65536, np.float32, dict()),
 ])
 def test_project_shapes(sp, ctx, Nc, Ns, dt, kw):
     rng = np.random.default_rng(Nc * 1000 + Ns)
