@@ -98,7 +98,12 @@ def test_grad_longest_grid_rows(sp, ctx):
     A0, R0, G0 = oracle.forces(K, grid)
     G, A, R = gpu_grad(sp, ctx, K, grid)
     assert_grad_close(A, A0, "A")
-    assert_grad_close(G, G0, "G")
+    assert_grad_close(R, R0, "R")
+    # uniform samples against a uniform-ish density: A and R nearly cancel,
+    # and G's relative error is A's and R's scaled by the subtraction's
+    # condition number (|A| + |R|) / (2 |G|)
+    cond = (np.linalg.norm(A0) + np.linalg.norm(R0)) / np.linalg.norm(G0) / 2
+    assert_grad_close(G, G0, f"G (condition {cond:.0f})", rel=1e-5 * max(cond, 1.0))
 
 
 def test_grad_many_source_blocks_and_tiles(sp, ctx):
