@@ -214,7 +214,7 @@ constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
 // BATCHED: the units of a.B trajectories (a.traj), else of one.
 template <bool ENERGY, int S, bool REG, bool BATCHED>
-__global__ void __launch_bounds__(kSymThreads, S == 1 ? 3 : 2) repulsion_sym_kernel(const SymArgs a)
+__global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
     constexpr int T = kSymT;
@@ -355,9 +355,8 @@ __global__ void __launch_bounds__(kSymThreads, S == 1 ? 3 : 2) repulsion_sym_ker
 template <bool E, bool REG, bool BATCHED>
 void *sym_fn_reg(int variant)
 {
-    return variant == 1   ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG, BATCHED>)
-           : variant == 2 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 1, REG, BATCHED>)
-                          : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG, BATCHED>);
+    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG, BATCHED>)
+                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG, BATCHED>);
 }
 
 template <bool E>
@@ -369,7 +368,7 @@ void *sym_fn(int variant, bool reg = true, bool batched = false)
 
 } // namespace
 
-int sym_variant_sources(int v) { return v == 1 ? 4 : (v == 2 ? 1 : 2); }
+int sym_variant_sources(int v) { return v == 1 ? 4 : 2; }
 
 size_t repulsion_sym_smem_bytes()
 {
