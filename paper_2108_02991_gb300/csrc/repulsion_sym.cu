@@ -94,7 +94,6 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
             sm[s] = ok ? 1.f : 0.f;
             bx[s] = 0.f; by[s] = 0.f; bz[s] = 0.f;
         }
-#pragma unroll 1
         for (int step = 0; step < 32; ++step) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -215,7 +214,7 @@ constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
 // BATCHED: the units of a.B trajectories (a.traj), else of one.
 template <bool ENERGY, int S, bool REG, bool BATCHED>
-__global__ void __launch_bounds__(kSymThreads, 3) repulsion_sym_kernel(const SymArgs a)
+__global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
     constexpr int T = kSymT;
