@@ -3,19 +3,21 @@
 // independent trajectories of uneven size.
 //
 // The host builds a work list (api.cu): for every trajectory and every tile
-// of 1024 targets, attraction items (a run of grid rows) and repulsion items
-// (a run of source blocks), then one projection item per shot.  Every CTA of
-// a single wave pulls the next item from a global counter.  Consecutive
-// attraction and repulsion items land on different CTAs, so each SM runs
-// SFU-bound attraction CTAs and issue-bound repulsion CTAs side by side.
+// of 1024 targets, attraction items (a run of grid rows), then one
+// projection item per shot.  The repulsion of every trajectory is summed
+// before the launch by the batched symmetric kernel (exact fixed-point
+// totals per sample, read through EngineArgs::racc); contexts where that
+// kernel cannot be resident get directed repulsion items (a run of source
+// blocks) interleaved with the attraction items instead.  Every CTA of a
+// single wave pulls the next item from a global counter.
 //
 // A pair item writes the FP64 partial sums of its tile into its own slot and
 // then bumps its trajectory's completion counter.  A projection item waits
 // (bounded) until its trajectory's counter reaches the number of pair items,
-// adds the slots of each sample in a fixed order (A - R/N), steps
-// k = K - eta G and projects the shot in place.  Because every item owns its
-// slot and the slots are added in a fixed order, results do not depend on
-// which CTA ran which item.
+// adds the slots of each sample in a fixed order (A - R/N, R from racc when
+// set), steps k = K - eta G and projects the shot in place.  Because every
+// item owns its slot and the slots are added in a fixed order, results do
+// not depend on which CTA ran which item.
 //
 // All items are dispensed in list order and all pair items precede all
 // projection items, so when a CTA waits on a trajectory every item it waits
