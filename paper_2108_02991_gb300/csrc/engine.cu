@@ -114,7 +114,10 @@ __device__ __forceinline__ RepArgs rep_args(const EngineTraj &t, const EngineArg
 
 // NT threads per CTA: 256 (4 targets per thread, repulsion unroll 4, three
 // CTAs per SM) or 512 (2 targets per thread, unroll 2, two CTAs per SM).
-template <int ACC, typename KT, int NT>
+// REP: the work list may hold directed repulsion items (only when the
+// batched symmetric kernel cannot run); without them the kernel carries no
+// repulsion code.
+template <int ACC, typename KT, int NT, bool REP>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const EngineArgs e)
 {
     extern __shared__ __align__(128) unsigned char esm[];
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
                                                 bars, accbase, consumed))
                 return;
             mark_done(e.done + item.traj);
-        } else if (item.kind == kItemRepulsion) {
+        } else if (REP && item.kind == kItemRepulsion) {
             const RepArgs r = rep_args(tr, e);
             if (!repulsion_segment<ACC, false, NT, (NT >= 512 ? 2 : 4)>(r, item.tile, item.u0, item.u1, item.slot,
                                                reinterpret_cast<float4 *>(stage), bars, accbase,
@@ -203,19 +206,21 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
     }
 }
 
-template <int ACC, typename KT, int NT>
-void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT, NT>); }
+template <int ACC, typename KT, int NT, bool REP>
+void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT, NT, REP>); }
 
-template <int NT>
+template <int NT, bool REP>
 void *pick_engine_nt(int acc, int dtype)
 {
-    if (acc == 0) return dtype == 0 ? engine_fn<0, float, NT>() : engine_fn<0, double, NT>();
-    return dtype == 0 ? engine_fn<1, float, NT>() : engine_fn<1, double, NT>();
+    if (acc == 0) return dtype == 0 ? engine_fn<0, float, NT, REP>() : engine_fn<0, double, NT, REP>();
+    return dtype == 0 ? engine_fn<1, float, NT, REP>() : engine_fn<1, double, NT, REP>();
 }
 
-void *pick_engine(int acc, int dtype, int variant)
+void *pick_engine(int acc, int dtype, int variant, bool rep)
 {
-    return variant == 1 ? pick_engine_nt<512>(acc, dtype) : pick_engine_nt<256>(acc, dtype);
+    if (rep)
+        return variant == 1 ? pick_engine_nt<512, true>(acc, dtype) : pick_engine_nt<256, true>(acc, dtype);
+    return variant == 1 ? pick_engine_nt<512, false>(acc, dtype) : pick_engine_nt<256, false>(acc, dtype);
 }
 
 } // namespace
@@ -228,22 +233,26 @@ int engine_variant_threads(int v) { return v == 1 ? 512 : 256; }
 
 int engine_ctas_per_sm(int acc, int dtype, int variant)
 {
-    void *fn = pick_engine(acc, dtype, variant);
-    const size_t smem = engine_smem_bytes();
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, engine_variant_threads(variant),
-                                                      smem) != cudaSuccess)
-        return 0;
-    return n;
+    int best = 1 << 30;
+    for (int rep = 0; rep < 2; ++rep) {
+        void *fn = pick_engine(acc, dtype, variant, rep != 0);
+        const size_t smem = engine_smem_bytes();
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, engine_variant_threads(variant),
+                                                          smem) != cudaSuccess)
+            return 0;
+        best = n < best ? n : best;
+    }
+    return best;
 }
 
 cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int variant, int ctas,
                           cudaStream_t st)
 {
-    void *fn = pick_engine(acc, dtype, variant);
+    void *fn = pick_engine(acc, dtype, variant, e.racc == nullptr);
     void *args[] = {const_cast<EngineArgs *>(&e)};
     return cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(engine_variant_threads(variant)), args,
                             engine_smem_bytes(), st);
