@@ -183,9 +183,10 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def measure_rsq_rate():
-    """Run alu_peak_probe.cu (built with nvcc) and return the measured
-    MUFU.RSQ results per SM per clock, or None when it cannot run."""
+def measure_probe():
+    """Run alu_peak_probe.cu (built with nvcc) and return its per-SM-per-clock
+    rates ({"rsqrt": .., "ffma": .., "dfma": .., "fp64acc": ..}), or {} when it
+    cannot run."""
     import re
     import shutil
     import tempfile
@@ -198,10 +199,16 @@ def measure_rsq_rate():
         r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
                             src], capture_output=True, text=True)
         if r.returncode != 0:
-            return None
+            return {}
         r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
-    m = re.search(r"^rsqrt\s+ops/SM/clk = ([0-9.]+)", r.stdout, re.M)
-    return float(m.group(1)) if m else None
+    rates = {}
+    for key, pat in (("rsqrt", r"^rsqrt\s"), ("ffma", r"^ffma\s"), ("attr_mix", r"^attr_mix"),
+                     ("dfma", r"^dfma\s"), ("fp64acc", r"^fp64acc")):
+        m = re.search(pat + r".*?ops/SM/clk = ([0-9.]+)", r.stdout, re.M)
+        if m:
+            rates[key] = float(m.group(1))
+    return rates
+
 
 
 # --- oracle timing (the CPU baseline and the reference arm) -------------------
@@ -398,7 +405,8 @@ def run_ours(args):
     except OSError:
         pass
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    rsq = measure_rsq_rate() if rank == 0 else None
+    probe = measure_probe() if rank == 0 else {}
+    rsq = probe.get("rsqrt")
     rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
     peak = sms * rate * max_mhz * 1e6
     if w.batched:
@@ -493,6 +501,7 @@ def run_ours(args):
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,
             "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
+            "alu_probe_per_sm_clk": probe or None,
         }
         if mesh_build_ms is not None:
             out["mesh"] = {
