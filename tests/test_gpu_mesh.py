@@ -165,3 +165,24 @@ def test_mesh_full_size_sampled_targets(sp, name, n_cells, m, sc, rs):
     # component at these grid sizes) and the mesh adds its own ~1e-6
     assert_grad_close(G.cpu().numpy()[idx], G0, f"G ({name}, mesh repulsion)", rel=2e-5,
                       atol=2e-5)
+
+
+@pytest.mark.parametrize("N", [2, 33])
+def test_mesh_tiny_sample_counts(sp, N):
+    """The smallest problems (one pair; a ragged handful) through the mesh
+    path: cell list, work items and mesh agree with the P3M oracle."""
+    n_cells, sc, rs = 16, 2.5, 4.0
+    K = np.random.default_rng(64 + N).uniform(-0.4, 0.4, size=(N, 3)).astype(np.float32)
+    K64 = K.astype(np.float64)
+    grid = inputs.density_gaussian(4, 0.2)
+    ctx = mesh_ctx(sp, n_cells, sc, rs)
+    try:
+        _, R, _ = gpu_grad(sp, ctx, K, grid)
+    finally:
+        ctx.close()
+    spec = p3m.MeshSpec(n_cells=n_cells, sigma=sc / n_cells, guard=guard(n_cells))
+    S, _, _, _ = oracle.repulsion_split(K64, spec.sigma, rc=rs * spec.sigma)
+    Lm, _ = p3m.mesh_long(K64, spec)
+    assert_grad_close(R, (S + Lm) / N, f"R (mesh, N = {N}) vs the P3M oracle", rel=3e-6, atol=2e-6)
+    _, R0, _ = oracle.forces(K64, grid)
+    assert rel_l2(R, R0) < 1e-5
