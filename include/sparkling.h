@@ -228,14 +228,17 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
                                  const sparkling_proj *proj, void *stream);
 
 /* One projected-gradient step K_b <- Pi(K_b - eta_b G(K_b)) for B
- * independent trajectories of uneven size in ONE persistent kernel launch
- * (plus the packing of samples and densities): a work list of attraction
- * items (a tile of 1024 targets against a run of grid rows) and repulsion
- * items (against a run of source blocks), interleaved so that each SM mixes
- * SFU-bound and issue-bound work, followed by one projection item per shot
- * that waits (bounded) for its trajectory's pair items.  Same arithmetic as
- * sparkling_step: FP32 pairs, acc per-target folds, FP64 gradient, step and
- * projection (fixed n_iter; converged mode is not available here).
+ * independent trajectories of uneven size in two launches (plus the packing
+ * of samples and densities): the symmetric repulsion of every trajectory
+ * (each unordered pair once, exact fixed-point totals), then one persistent
+ * kernel that runs a work list of attraction items (a tile of 1024 targets
+ * against a run of grid rows) followed by one projection item per shot that
+ * waits (bounded) for its trajectory's attraction items.  (Where the
+ * symmetric kernel cannot be resident the repulsion runs as directed items
+ * of the same work list.)  Same arithmetic as sparkling_step: FP32 pairs,
+ * acc per-target folds, FP64 gradient, step and projection (fixed n_iter;
+ * converged mode is not available here); the context's regularisation
+ * applies, its attraction and repulsion modes do not (direct sums).
  *   traj_off  host [B+1]: trajectory b is samples [traj_off[b], traj_off[b+1])
  *             of K; traj_off[0] = 0; every trajectory holds >= 2 samples and
  *             a whole number of shots of Ns samples
