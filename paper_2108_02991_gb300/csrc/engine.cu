@@ -114,6 +114,62 @@ __device__ __forceinline__ RepArgs rep_args(const EngineTraj &t, const EngineArg
 
 // NT threads per CTA: 256 (4 targets per thread, repulsion unroll 4, three
 // CTAs per SM) or 512 (2 targets per thread, unroll 2, two CTAs per SM).
+// A projection item (one shot), out of line so that its registers do not
+// crowd the attraction loop of the kernel: wait (bounded) for the
+// trajectory's pair items, form k = K - eta G from the slots and the
+// symmetric repulsion totals, and project the shot in place.
+template <typename KT>
+__device__ __noinline__ bool project_item(const EngineArgs &e, const EngineItem &item,
+                                          const EngineTraj &tr, unsigned char *region, int *bcast)
+{
+    if (!wait_done(e.done + item.traj, (unsigned int)tr.n_pair_items, e.status, bcast + 1))
+        return false;
+    const int Ns = tr.Ns;
+    double *base = e.proj_in_smem ? reinterpret_cast<double *>(region)
+                                  : e.gstate + (size_t)blockIdx.x * 18 * (size_t)Ns;
+    const Arrays A = carve(base, Ns);
+    ShotParams sp;
+    sp.Ns = Ns;
+    sp.alpha = tr.alpha; sp.beta = tr.beta; sp.box = tr.box;
+    sp.tol = 0.0; sp.margin = 0.0;
+    for (int c = 0; c < 3; ++c) sp.pin[c] = tr.pin[c];
+    sp.pin_index = tr.pin_index; sp.n_iter = tr.n_iter; sp.check_every = 0;
+    sp.viol = nullptr; sp.notconv = nullptr;
+    const int64_t first = (int64_t)item.tile * Ns;          // local sample index
+    KT *K = static_cast<KT *>(e.K) + 3 * (tr.off + first);
+    const dacc4 *part = e.part + tr.part_off;
+    const double invN = 1.0 / (double)tr.N;
+    const double eta = tr.eta;
+    const int slots = tr.slots, ach = tr.a_chunks;
+    auto loadk = [&](int m, double *kv) {
+        const int64_t i = first + m;
+        const int64_t tile = i / kTile, l = i - tile * kTile;
+        const dacc4 *p = part + tile * slots * kTile + l;
+        double g[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < slots; ++s) {
+            const double2 xy = __ldcg(reinterpret_cast<const double2 *>(p + s * kTile));
+            const double zz = __ldcg(reinterpret_cast<const double *>(p + s * kTile) + 2);
+            if (s < ach) { g[0] += xy.x; g[1] += xy.y; g[2] += zz; }
+            else { r[0] += xy.x; r[1] += xy.y; r[2] += zz; }
+        }
+        if (e.racc) {   // symmetric repulsion totals (fixed point), written before the launch
+            const unsigned long long *q = e.racc + 3 * (tr.off + i);
+            for (int c = 0; c < 3; ++c) r[c] = (double)(long long)__ldcg(q + c) / kFixScale;
+        }
+        for (int c = 0; c < 3; ++c)
+            kv[c] = (double)K[3 * m + c] - eta * (g[c] - r[c] * invN);
+    };
+    if (sizeof(KT) == 4)
+        project_shot_mixed<KT>(carve_f(reinterpret_cast<float *>(base), Ns), K, sp, loadk);
+    else
+        project_shot<KT>(A, K, sp, loadk);
+    // The projection state may share memory with the stage buffers: order its
+    // ordinary stores before later bulk copies (async proxy).
+    fence_proxy_async_smem();
+    __syncthreads();
+    return true;
+}
+
 // REP: the work list may hold directed repulsion items (only when the
 // batched symmetric kernel cannot run); without them the kernel carries no
 // repulsion code.
@@ -157,51 +213,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
                 return;
             mark_done(e.done + item.traj);
         } else {
-            if (!wait_done(e.done + item.traj, (unsigned int)tr.n_pair_items, e.status, bcast + 1))
+            if (!project_item<KT>(e, item, tr, region, bcast))
                 return;
-            const int Ns = tr.Ns;
-            double *base = e.proj_in_smem ? reinterpret_cast<double *>(region)
-                                          : e.gstate + (size_t)blockIdx.x * 18 * (size_t)Ns;
-            const Arrays A = carve(base, Ns);
-            ShotParams sp;
-            sp.Ns = Ns;
-            sp.alpha = tr.alpha; sp.beta = tr.beta; sp.box = tr.box;
-            sp.tol = 0.0; sp.margin = 0.0;
-            for (int c = 0; c < 3; ++c) sp.pin[c] = tr.pin[c];
-            sp.pin_index = tr.pin_index; sp.n_iter = tr.n_iter; sp.check_every = 0;
-            sp.viol = nullptr; sp.notconv = nullptr;
-            const int64_t first = (int64_t)item.tile * Ns;          // local sample index
-            KT *K = static_cast<KT *>(e.K) + 3 * (tr.off + first);
-            const dacc4 *part = e.part + tr.part_off;
-            const double invN = 1.0 / (double)tr.N;
-            const double eta = tr.eta;
-            const int slots = tr.slots, ach = tr.a_chunks;
-            auto loadk = [&](int m, double *kv) {
-                const int64_t i = first + m;
-                const int64_t tile = i / kTile, l = i - tile * kTile;
-                const dacc4 *p = part + tile * slots * kTile + l;
-                double g[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
-                for (int s = 0; s < slots; ++s) {
-                    const double2 xy = __ldcg(reinterpret_cast<const double2 *>(p + s * kTile));
-                    const double zz = __ldcg(reinterpret_cast<const double *>(p + s * kTile) + 2);
-                    if (s < ach) { g[0] += xy.x; g[1] += xy.y; g[2] += zz; }
-                    else { r[0] += xy.x; r[1] += xy.y; r[2] += zz; }
-                }
-                if (e.racc) {   // symmetric repulsion totals (fixed point), written before the launch
-                    const unsigned long long *q = e.racc + 3 * (tr.off + i);
-                    for (int c = 0; c < 3; ++c) r[c] = (double)(long long)__ldcg(q + c) / kFixScale;
-                }
-                for (int c = 0; c < 3; ++c)
-                    kv[c] = (double)K[3 * m + c] - eta * (g[c] - r[c] * invN);
-            };
-            if (sizeof(KT) == 4)
-                project_shot_mixed<KT>(carve_f(reinterpret_cast<float *>(base), Ns), K, sp, loadk);
-            else
-                project_shot<KT>(A, K, sp, loadk);
-            // The projection state may share memory with the stage buffers:
-            // order its ordinary stores before later bulk copies (async proxy).
-            fence_proxy_async_smem();
-            __syncthreads();
         }
     }
 }
