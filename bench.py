@@ -68,6 +68,13 @@ def parse_args(argv=None):
                     help="split width in mesh cells for --repulsion mesh")
     ap.add_argument("--mesh-rc", type=float, default=3.5,
                     help="short-range cut-off in split widths for --repulsion mesh")
+    ap.add_argument("--shape-attraction", type=int, default=-1,
+                    help="pin the attraction's tile shape (0/1/2: 128/256/512 threads; "
+                         "-1: autotuned)")
+    ap.add_argument("--shape-repulsion", type=int, default=-1,
+                    help="pin the symmetric repulsion's tile shape (0: 2 sources per lane, "
+                         "targets paired; 1: 4 sources, targets paired; 2: 2 sources, sources "
+                         "paired; -1: autotuned)")
     ap.add_argument("--clock-log", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: the temp dir)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -344,6 +351,10 @@ def run_ours(args):
     w = Workload(sp, args, dev, seed=rank)
     ctx = sp.sparkling_create(local)
     w.ctx = ctx
+    if args.shape_attraction >= 0:
+        sp.sparkling_set_shape(ctx, "attraction", args.shape_attraction)
+    if args.shape_repulsion >= 0:
+        sp.sparkling_set_shape(ctx, "repulsion", args.shape_repulsion)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     field_build_ms = None
@@ -496,7 +507,11 @@ def run_ours(args):
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
                        "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
                        "l2": "flushed (512 MB write) between timed steps", "acc": args.acc,
-                       "attraction": args.attraction, "repulsion": args.repulsion},
+                       "attraction": args.attraction, "repulsion": args.repulsion,
+                       "shapes": ("autotuned" if args.shape_attraction < 0
+                                  and args.shape_repulsion < 0 else
+                                  f"pinned: attraction {args.shape_attraction}, "
+                                  f"repulsion {args.shape_repulsion} (-1: autotuned)")},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,

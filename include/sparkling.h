@@ -321,6 +321,19 @@ SPARKLING_API int sparkling_kernel_times(sparkling_ctx *ctx, double *ms_out, int
  * stream that is being captured. */
 SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
 
+/* Pin the tile shape of one pair kernel for the context's later calls
+ * (reproducible timing; the tests run every shape through it), instead of
+ * the autotuner's choice.  kernel = SPARKLING_KERNEL_ATTRACTION: variant 0,
+ * 1, 2 = 128, 256, 512 threads per CTA (8, 4, 2 targets per thread).
+ * kernel = SPARKLING_KERNEL_REPULSION (the symmetric kernel of
+ * sparkling_grad, sparkling_energy, sparkling_step and the batched step):
+ * variant 0 = 2 sources per lane, targets paired in the 64-bit registers;
+ * 1 = 4 sources per lane, targets paired; 2 = 2 sources per lane, the two
+ * sources paired.  variant = -1 unpins (the next call of a new key tunes
+ * again when the autotuner is on).  sparkling_set_autotune(ctx, -1) unpins
+ * both.  Returns SPARKLING_E_INVAL for another kernel or variant. */
+SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int variant);
+
 /* Text of the tuning trials (pairs/s per shape) and of the choices, NUL
  * terminated, truncated to len bytes. */
 SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, int64_t len);

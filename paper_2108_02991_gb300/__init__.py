@@ -32,6 +32,7 @@ ABI_SYMBOLS = (
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
     "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
     "sparkling_upsample", "sparkling_optimize", "sparkling_multires", "sparkling_set_repulsion",
+    "sparkling_set_shape",
 )
 
 
@@ -118,6 +119,7 @@ def lib() -> ctypes.CDLL:
             "sparkling_version": ([], ctypes.c_char_p),
             "sparkling_grad_noalloc": ([p, i, i64, ctypes.POINTER(Grid), i, p, i, p], i),
             "sparkling_set_autotune": ([p, i], i),
+            "sparkling_set_shape": ([p, i, i], i),
             "sparkling_tuning_report": ([p, p, i64], i),
             "sparkling_set_attraction": ([p, i], i),
             "sparkling_attraction_field": ([p, p, p], i),
@@ -367,6 +369,13 @@ def sparkling_kernel_times(ctx: Context, reset: bool = False):
 def sparkling_set_autotune(ctx: Context, enable: int = 1) -> None:
     """1: tune tile shapes at first use (default); 0: default shapes; -1: retune."""
     _check(ctx, lib().sparkling_set_autotune(ctx.handle, int(enable)))
+
+
+def sparkling_set_shape(ctx: Context, kernel: str, variant: int) -> None:
+    """Pin the tile shape of "attraction" (0/1/2: 128/256/512 threads) or of
+    the symmetric "repulsion" (0: 2 sources per lane, targets paired; 1: 4
+    sources, targets paired; 2: 2 sources, sources paired); -1 unpins."""
+    _check(ctx, lib().sparkling_set_shape(ctx.handle, KERNEL_NAMES.index(kernel), int(variant)))
 
 
 def sparkling_tuning_report(ctx: Context) -> str:

@@ -53,6 +53,7 @@ struct sparkling_ctx {
     bool rep_symmetric = true;     // repulsion: symmetric kernel (else the directed shapes)
     int occ_sym[2][kSymVariants] = {};
     int sym_choice = -1;           // sources per lane of the symmetric kernel (variant)
+    int pin_attr = -1;             // attraction shape pinned by sparkling_set_shape
     std::string tune_log;
     // batched step: cached work list, workspace layout and CUDA graph
     struct Batch {
@@ -322,6 +323,7 @@ int ensure_occupancy(sparkling_ctx *ctx)
 
 int attr_choice_of(const sparkling_ctx *ctx, int acc, int gxp)
 {
+    if (ctx->pin_attr >= 0) return ctx->pin_attr;
     const int64_t key = (int64_t)acc * (1 << 20) + gxp;
     for (const auto &kv : ctx->attr_choice)
         if (kv.first == key) return kv.second;
@@ -334,6 +336,7 @@ void set_splits(sparkling_ctx *ctx, PairPlan &P, int acc, bool energy, int va, i
     const int e = energy ? 1 : 0;
     const int64_t rows = (int64_t)P.ny * P.nz;
     const int64_t nblocks = (P.N + kSrcBlock - 1) / kSrcBlock;
+    if (ctx->occ_attr[acc][e][va] < 1) va = kAttrDefault;   // a pinned shape that cannot be resident
     P.va = va;
     P.vr = vr;
     P.spa = make_split(P.tiles, rows, (int64_t)ctx->sms * ctx->occ_attr[acc][e][va]);
@@ -453,15 +456,16 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
         SymArgs sa{};
         sa.pos = ra.pos; sa.N = std::min<int64_t>(P.N, tt * kTile); sa.tiles = tt;
         sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2;
-        int best = 0;
+        int best = kSymDefault;
         double best_rate = 0.0;
         for (int v = 0; v < kSymVariants; ++v) {
             sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[0][v];
             const double ms = timed([&] { return launch_repulsion_sym(sa, false, v, st); });
             const double pairs = (double)sa.N * (double)(sa.N - 1);
             const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
-            snprintf(line, sizeof line, "repulsion symmetric sources/lane=%d: %.4g pairs/s\n",
-                     sym_variant_sources(v), rate);
+            snprintf(line, sizeof line, "repulsion symmetric sources/lane=%d %s-paired: %.4g pairs/s\n",
+                     sym_variant_sources(v), sym_variant_source_paired(v) ? "source" : "target",
+                     rate);
             ctx->tune_log += line;
             if (rate > best_rate) { best_rate = rate; best = v; }
         }
@@ -644,7 +648,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         racc = at<unsigned long long>(ctx, P.o_racc);
         SymArgs sa{};
         sa.pos = pos; sa.N = P.N; sa.tiles = P.tiles;
-        const int sv = ctx->sym_choice < 0 ? 0 : ctx->sym_choice;
+        const int sv = ctx->sym_choice < 0 ? kSymDefault : ctx->sym_choice;
         sa.ctas = (int64_t)ctx->sms * ctx->occ_sym[energy ? 1 : 0][sv];
         sa.acc = racc; sa.status = ctx->d_status; sa.eps2 = ra.eps2;
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
@@ -968,7 +972,7 @@ int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_
         sa.traj = at<SymTraj>(ctx, b.o_symtraj);
         sa.B = b.B;
         sa.units = b.sym_units;
-        const int sv = ctx->sym_choice < 0 ? 0 : ctx->sym_choice;
+        const int sv = ctx->sym_choice < 0 ? kSymDefault : ctx->sym_choice;
         sa.ctas = std::min<int64_t>((int64_t)ctx->sms * ctx->occ_sym[0][sv], b.sym_units);
         CK(launch_repulsion_sym(sa, false, sv, st));
     }
@@ -1613,10 +1617,31 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable)
         ctx->rep_choice[0] = ctx->rep_choice[1] = -1;
         for (auto &row : ctx->engine_choice) row[0] = row[1] = -1;
         ctx->sym_choice = -1;
+        ctx->pin_attr = -1;
         ctx->tune_log.clear();
         ctx->autotune = true;
     }
     return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int variant)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (kernel == SPARKLING_KERNEL_ATTRACTION) {
+        if (variant < -1 || variant >= kAttrVariants)
+            return fail(ctx, SPARKLING_E_INVAL, "attraction shape %d not in -1..%d", variant,
+                        kAttrVariants - 1);
+        ctx->pin_attr = variant;
+        return SPARKLING_OK;
+    }
+    if (kernel == SPARKLING_KERNEL_REPULSION) {
+        if (variant < -1 || variant >= kSymVariants)
+            return fail(ctx, SPARKLING_E_INVAL, "repulsion shape %d not in -1..%d", variant,
+                        kSymVariants - 1);
+        ctx->sym_choice = variant;
+        return SPARKLING_OK;
+    }
+    return fail(ctx, SPARKLING_E_INVAL, "kernel %d has no selectable shape", kernel);
 }
 
 SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode)
@@ -1692,8 +1717,9 @@ SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, i
         }
     if (ctx->sym_choice >= 0) {
         char line[128];
-        snprintf(line, sizeof line, "chosen repulsion symmetric: sources/lane=%d\n",
-                 sym_variant_sources(ctx->sym_choice));
+        snprintf(line, sizeof line, "chosen repulsion symmetric: sources/lane=%d %s-paired\n",
+                 sym_variant_sources(ctx->sym_choice),
+                 sym_variant_source_paired(ctx->sym_choice) ? "source" : "target");
         r += line;
     }
     const size_t n = std::min<size_t>(r.size(), (size_t)len - 1);

@@ -177,8 +177,10 @@ int repulsion_ctas_per_sm(int acc, bool energy, int variant);
 cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st);
 // Symmetric repulsion (repulsion_sym.cu): every unordered pair once.
-constexpr int kSymVariants = 2;       // sources per lane 2 / 4
+constexpr int kSymVariants = 3;       // sources per lane 2 / 4 (target-paired), 2 (source-paired)
+constexpr int kSymDefault = 2;        // shape used where nothing was tuned or pinned
 int sym_variant_sources(int v);
+bool sym_variant_source_paired(int v);
 size_t repulsion_sym_smem_bytes();
 int repulsion_sym_ctas_per_sm(bool energy, int variant);
 cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st);

@@ -7,13 +7,16 @@
 // Work: the upper triangle of tile pairs (I, J), I <= J, tiles of 1024
 // samples, split evenly over one wave of persistent CTAs (contiguous runs of
 // a row share the target tile I).  In a CTA, warp w holds 128 targets of
-// tile I (4 per lane) and, in round r, the 128 sources of chunk (w + r) mod 8
-// of tile J (4 per lane, staged by a TMA bulk copy).  The sources and their
-// accumulators rotate one lane per step through the 32 lanes, so after 32
-// steps every (target, source) pair of the two chunks has met once and each
-// source is back home; its accumulator is then added to a shared-memory
-// j-accumulator, which no other warp touches in that round.  A diagonal pair
-// (I, I) is evaluated directed (targets only).
+// tile I (4 per lane) and, in round r, the 32*S sources of chunk
+// (w + r) mod (1024 / 32S) of tile J (S per lane, the tile staged by a TMA
+// bulk copy).  The sources and their accumulators rotate one lane per step
+// through the 32 lanes, so after 32 steps every (target, source) pair of the
+// two chunks has met once and each source is back home; its accumulator is
+// then added to a shared-memory j-accumulator, which no other warp touches
+// in that round.  A diagonal pair (I, I) is evaluated directed (targets
+// only).  The pair arithmetic is paired FP32 (f32x2): either two targets
+// share a 64-bit register (sym_item, S = 2 or 4) or a lane's two sources do
+// (sym_item_sp, S = 2).
 //
 // Totals are kept as fixed-point integers (x * 2^32 in int64) and added with
 // 64-bit atomics: integer addition is exact and order-independent, so the
@@ -179,6 +182,107 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
     }
 }
 
+// The same item with the pairing turned around: a lane's two sources
+// (c*64 + lane and c*64 + 32 + lane of chunk c) share the 64-bit registers,
+// and each target is copied into both halves once per item.  A step then
+// needs no packing and no folding: per target, 3 differences, 3 squared-
+// distance steps and 3 + 3 accumulations, all paired -- 12 FP32 lane
+// operations per unordered pair -- and the source sums stay paired while
+// they rotate.  The target sums are folded once per item.
+template <bool ENERGY, bool RAGGED>
+__device__ __forceinline__ void sym_item_sp(const float4 *src, int jvalid, const float *tx,
+                                            const float *ty, const float *tz, const float *tm,
+                                            float eps2, float (*ai)[3], float *jacc)
+{
+    constexpr int T = kSymT;
+    constexpr int kChunk = 64, kChunks = kTile / kChunk;
+    static_assert(kChunks >= kSymWarps && (kChunks & (kChunks - 1)) == 0, "chunk count");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int from = (lane + 1) & 31;
+    f2 TX[T], TY[T], TZ[T], TM[T], AX[T], AY[T], AZ[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        TX[t] = f2_pack(tx[t], tx[t]);
+        TY[t] = f2_pack(ty[t], ty[t]);
+        TZ[t] = f2_pack(tz[t], tz[t]);
+        TM[t] = f2_pack(tm[t], tm[t]);
+        AX[t] = AY[t] = AZ[t] = f2_pack(0.f, 0.f);
+    }
+    const f2 E2 = f2_pack(eps2, eps2);
+    for (int r = 0; r < kChunks; ++r) {
+        const int c = (warp + r) & (kChunks - 1);
+        const int j0 = c * kChunk + lane, j1 = j0 + 32;
+        // a missing source (stale shared memory, possibly NaN) becomes a
+        // finite point whose terms the zero mask then removes
+        const bool ok0 = !RAGGED || j0 < jvalid, ok1 = !RAGGED || j1 < jvalid;
+        const float4 q0 = ok0 ? src[j0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q1 = ok1 ? src[j1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        f2 SX = f2_pack(q0.x, q1.x), SY = f2_pack(q0.y, q1.y), SZ = f2_pack(q0.z, q1.z);
+        f2 SM = f2_pack(ok0 ? 1.f : 0.f, ok1 ? 1.f : 0.f);
+        f2 BX = f2_pack(0.f, 0.f), BY = BX, BZ = BX;     // + the pair terms of the two sources
+        for (int step = 0; step < 32; ++step) {
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const f2 DX = f2_sub(TX[t], SX), DY = f2_sub(TY[t], SY), DZ = f2_sub(TZ[t], SZ);
+                const f2 R2 = f2_fma(DX, DX, f2_fma(DY, DY, f2_fma(DZ, DZ, E2)));
+                float r2a, r2b;
+                f2_unpack(R2, r2a, r2b);
+                f2 RI = f2_pack(rsqrt_sfu(r2a), rsqrt_sfu(r2b));
+                if (RAGGED) RI = f2_mul(RI, f2_mul(SM, TM[t]));
+                if (ENERGY) {
+                    const f2 E = f2_mul(R2, RI);      // |d|, counted for both samples
+                    AX[t] = f2_add(AX[t], E);
+                    BX = f2_add(BX, E);
+                } else {
+                    AX[t] = f2_fma(DX, RI, AX[t]);
+                    AY[t] = f2_fma(DY, RI, AY[t]);
+                    AZ[t] = f2_fma(DZ, RI, AZ[t]);
+                    BX = f2_fma(DX, RI, BX);
+                    BY = f2_fma(DY, RI, BY);
+                    BZ = f2_fma(DZ, RI, BZ);
+                }
+            }
+            // the sources and their sums move one lane down
+            SX = __shfl_sync(0xffffffffu, SX, from);
+            SY = __shfl_sync(0xffffffffu, SY, from);
+            SZ = __shfl_sync(0xffffffffu, SZ, from);
+            if (RAGGED) SM = __shfl_sync(0xffffffffu, SM, from);
+            BX = __shfl_sync(0xffffffffu, BX, from);
+            if (!ENERGY) {
+                BY = __shfl_sync(0xffffffffu, BY, from);
+                BZ = __shfl_sync(0xffffffffu, BZ, from);
+            }
+        }
+        // back home after 32 steps; this warp alone owns chunk c in round r.
+        // The pair term is odd: a source's force share is minus the sum.
+        float u, v;
+        f2_unpack(BX, u, v);
+        jacc[j0] += ENERGY ? u : -u;
+        jacc[j1] += ENERGY ? v : -v;
+        if (!ENERGY) {
+            f2_unpack(BY, u, v);
+            jacc[kTile + j0] -= u;
+            jacc[kTile + j1] -= v;
+            f2_unpack(BZ, u, v);
+            jacc[2 * kTile + j0] -= u;
+            jacc[2 * kTile + j1] -= v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        float u, v;
+        f2_unpack(AX[t], u, v);
+        ai[t][0] += u + v;
+        if (!ENERGY) {
+            f2_unpack(AY[t], u, v);
+            ai[t][1] += u + v;
+            f2_unpack(AZ[t], u, v);
+            ai[t][2] += u + v;
+        }
+    }
+}
+
 // A diagonal item (I, I): the thread's targets against every source of the
 // tile, directed (each ordered pair once, target side only; the self term
 // contributes nothing to the force and eps to the energy, which the energy
@@ -213,7 +317,9 @@ constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
 // REG: the regularisation eps^2 is a kernel argument; without it the
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
 // BATCHED: the units of a.B trajectories (a.traj), else of one.
-template <bool ENERGY, int S, bool REG, bool BATCHED>
+// SP: the source-paired item (two sources per lane), else the target-paired
+// item with S sources per lane.
+template <bool ENERGY, int S, bool SP, bool REG, bool BATCHED>
 __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
@@ -326,10 +432,17 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
         } else {
             for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
             __syncthreads();
-            if (jvalid < kTile)
-                sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
-            else
-                sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+            if (SP) {
+                if (jvalid < kTile)
+                    sym_item_sp<ENERGY, true>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                else
+                    sym_item_sp<ENERGY, false>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+            } else {
+                if (jvalid < kTile)
+                    sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                else
+                    sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+            }
             for (int l = tid; l < jvalid; l += kSymThreads)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -355,8 +468,9 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
 template <bool E, bool REG, bool BATCHED>
 void *sym_fn_reg(int variant)
 {
-    return variant == 1 ? reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, REG, BATCHED>)
-                        : reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, REG, BATCHED>);
+    if (variant == 1) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, false, REG, BATCHED>);
+    if (variant == 2) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, true, REG, BATCHED>);
+    return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, false, REG, BATCHED>);
 }
 
 template <bool E>
@@ -369,6 +483,7 @@ void *sym_fn(int variant, bool reg = true, bool batched = false)
 } // namespace
 
 int sym_variant_sources(int v) { return v == 1 ? 4 : 2; }
+bool sym_variant_source_paired(int v) { return v == 2; }
 
 size_t repulsion_sym_smem_bytes()
 {

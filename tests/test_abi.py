@@ -143,6 +143,14 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert "margin" in msg
     assert L.sparkling_grad(None, dummy, 0, 10, ctypes.byref(g), 0, dummy, 0, None, None, None) == lib.E_INVAL
     assert "ctx" in lib.sparkling_last_error(None)
+    # pinned tile shapes
+    assert L.sparkling_set_shape(None, 1, 0) == lib.E_INVAL
+    assert L.sparkling_set_shape(h, 0, 0) == lib.E_INVAL          # pack has no shapes
+    assert L.sparkling_set_shape(h, 1, 3) == lib.E_INVAL
+    assert L.sparkling_set_shape(h, 2, 3) == lib.E_INVAL
+    assert L.sparkling_set_shape(h, 2, -2) == lib.E_INVAL
+    for k, v in ((1, 2), (1, -1), (2, 2), (2, -1)):
+        assert L.sparkling_set_shape(h, k, v) == lib.OK
     # attraction mode
     assert L.sparkling_set_attraction(h, 7) == lib.E_INVAL
     assert L.sparkling_set_attraction(h, lib.ATTRACTION_FIELD) == lib.OK
