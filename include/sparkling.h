@@ -329,7 +329,8 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
  * sparkling_grad, sparkling_energy, sparkling_step and the batched step):
  * variant 0 = 2 sources per lane, targets paired in the 64-bit registers;
  * 1 = 4 sources per lane, targets paired; 2 = 2 sources per lane, the two
- * sources paired.  variant = -1 unpins (the next call of a new key tunes
+ * sources paired (the shape used where nothing is tuned or pinned, e.g. by
+ * the batched step).  variant = -1 unpins (the next call of a new key tunes
  * again when the autotuner is on).  sparkling_set_autotune(ctx, -1) unpins
  * both.  Returns SPARKLING_E_INVAL for another kernel or variant. */
 SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int variant);
