@@ -52,7 +52,7 @@ struct sparkling_ctx {
     int rep_choice[2] = {-1, -1};
     bool rep_symmetric = true;     // repulsion: symmetric kernel (else the directed shapes)
     int occ_sym[2][kSymVariants] = {};
-    int sym_choice = -1;           // sources per lane of the symmetric kernel (variant)
+    int sym_choice = -1;           // shape of the symmetric kernel (tuned or pinned; -1: none)
     int pin_attr = -1;             // attraction shape pinned by sparkling_set_shape
     std::string tune_log;
     // batched step: cached work list, workspace layout and CUDA graph
