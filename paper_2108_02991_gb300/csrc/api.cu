@@ -1,9 +1,11 @@
 // C ABI of the SPARKLING GB300 library (declared in include/sparkling.h).
 //
 // Host-side orchestration only: argument validation, the device workspace,
-// the even work split of the pair kernels, launch bookkeeping (counts and
-// optional CUDA-event timing) and status reporting.  All arithmetic of the
-// hot path runs in the kernels of pairs.cu and project.cu.
+// the even work split of the pair kernels, the autotuner, the batched step's
+// work list and CUDA graph, the multi-resolution driver's loop and
+// checkpoints, launch bookkeeping (counts and optional CUDA-event timing) and
+// status reporting.  All arithmetic of the hot path runs in the kernels of
+// the other csrc/ files.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -1,5 +1,6 @@
-// Internal interface between the C-ABI layer (api.cu) and the kernels
-// (pairs.cu, project.cu).  Not installed; not part of the ABI.
+// Internal interface between the C-ABI layer (api.cu) and the kernel files
+// (pairs.cu, repulsion.cu, repulsion_sym.cu, project.cu, engine.cu,
+// field.cu, mesh.cu, driver.cu).  Not installed; not part of the ABI.
 #pragma once
 #include <cmath>
 #include <cstdint>
