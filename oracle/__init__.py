@@ -12,6 +12,8 @@ NumPy arrays.  See the C file for the definitions followed:
   repulsion_term, attraction_derivative_basic, Fr_grad with H = |.|_2);
 * ``energy``  -- F^a, F^r (eqs. global_minimization, attraction_term,
   repulsion_term);
+* ``energy_terms`` -- the terms of F that contain one sample, with that
+  sample moved (for central differences of F in one coordinate);
 * ``attraction_at`` -- attraction force and potential of the density at
   arbitrary points (the field of eq. attraction_derivative_basic);
 * ``project`` -- per-shot projection onto the constraint set (eq. constraints,
@@ -72,6 +74,8 @@ def _load():
             d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
             lib.oracle_forces.argtypes = [p, i64, p, i64, i64, i64, d, d, p, i64, p, p, p, p, p, d]
             lib.oracle_energy.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p, d]
+            lib.oracle_energy_terms.argtypes = [p, i64, p, i64, i64, i64, d, d, p, p, i64, p, p, d]
+            lib.oracle_energy_terms.restype = ctypes.c_int
             lib.oracle_project.argtypes = [p, p, i64, i64, d, d, d, i64, p, i64, d, d, i64, p]
             lib.oracle_violation.argtypes = [p, i64, i64, d, d, d, i64, p, p]
             lib.oracle_step.argtypes = [p, i64, i64, p, i64, i64, i64, d, d, d, d, d, d, i64, p, i64, d]
@@ -128,6 +132,25 @@ def forces(K, grid, targets=None, energies: bool = False, eps: float = 0.0):
     if st != OK:
         raise ValueError(f"oracle_forces failed ({st})")
     return (A, R, G, ea, er) if energies else (A, R, G)
+
+
+def energy_terms(K, grid, idx, points, eps: float = 0.0):
+    """(ea, er) for M pairs (idx[m], points[m]): the energy sums of sample
+    idx[m] moved to points[m] -- sum_q rho_q |p - x_q| and sum_{j != i}
+    |p - K_j|.  F depends on K_i only through ea / N - er / N^2."""
+    K = _f64(K)
+    rho, nx, ny, nz, lo, hi = _grid_args(grid)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
+    P = _f64(points).reshape(-1, 3)
+    if P.shape[0] != idx.size:
+        raise ValueError("one point per index")
+    ea = np.empty(idx.size)
+    er = np.empty(idx.size)
+    st = _load().oracle_energy_terms(_ptr(K), K.shape[0], _ptr(rho), nx, ny, nz, lo, hi,
+                                     _ptr(idx), _ptr(P), idx.size, _ptr(ea), _ptr(er), float(eps))
+    if st != OK:
+        raise ValueError(f"oracle_energy_terms failed ({st})")
+    return ea, er
 
 
 def attraction_at(points, grid, eps: float = 0.0):

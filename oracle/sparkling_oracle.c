@@ -86,15 +86,14 @@ static void attraction_one(double kx, double ky, double kz, const double *rho,
     *energy = e;
 }
 
-/* Sum over j != i of the unit vectors (K_i - K_j)/|K_i - K_j| and of the
- * distances |K_i - K_j| (not yet scaled by 1/N). */
-static void repulsion_one(const double *K, int64_t N, int64_t i, double eps, double out[3],
-                          double *energy)
+/* Sum over j != skip of the unit vectors (p - K_j)/|p - K_j| and of the
+ * distances |p - K_j| for a point p = (kx, ky, kz) (not yet scaled by 1/N). */
+static void repulsion_at(const double *K, int64_t N, int64_t skip, double kx, double ky,
+                         double kz, double eps, double out[3], double *energy)
 {
-    double kx = K[3 * i], ky = K[3 * i + 1], kz = K[3 * i + 2];
     double rx = 0.0, ry = 0.0, rz = 0.0, e = 0.0;
     for (int64_t j = 0; j < N; ++j) {
-        if (j == i)
+        if (j == skip)
             continue;
         double dx = kx - K[3 * j], dy = ky - K[3 * j + 1], dz = kz - K[3 * j + 2];
         double r = sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
@@ -107,6 +106,13 @@ static void repulsion_one(const double *K, int64_t N, int64_t i, double eps, dou
     }
     out[0] = rx; out[1] = ry; out[2] = rz;
     *energy = e;
+}
+
+/* The same sums for sample i at its own position K_i. */
+static void repulsion_one(const double *K, int64_t N, int64_t i, double eps, double out[3],
+                          double *energy)
+{
+    repulsion_at(K, N, i, K[3 * i], K[3 * i + 1], K[3 * i + 2], eps, out, energy);
 }
 
 /*
@@ -161,6 +167,37 @@ int oracle_attraction_at(const double *P, int64_t M, const double *rho, int64_t 
         if (phi) phi[m] = e;
     }
     return ORACLE_OK;
+}
+
+/* The terms of F that contain one sample, with that sample moved: for M
+ * pairs (idx[m], P[m]), sample i = idx[m] placed at the point p = P[m]:
+ *   ea[m] = sum_q rho_q |p - x_q|,   er[m] = sum_{j != i} |p - K_j|.
+ * In eq. global_minimization only (1/N) ea - (1/N^2) er depends on K_i (the
+ * repulsion's double sum holds each pair twice), so central differences of
+ * it in one coordinate of p give dF/dK_i without subtracting two energies of
+ * size O(1).  OpenMP splits the M pairs. */
+int oracle_energy_terms(const double *K, int64_t N, const double *rho, int64_t nx, int64_t ny,
+                        int64_t nz, double lo, double hi, const int64_t *idx, const double *P,
+                        int64_t M, double *ea, double *er, double eps)
+{
+    if (!K || N < 1 || !rho || nx < 1 || ny < 1 || nz < 1 || !(hi > lo) || M < 0 || !idx ||
+        !P || !ea || !er || !(eps >= 0.0))
+        return ORACLE_EINVAL;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+    for (int64_t m = 0; m < M; ++m) {
+        const int64_t i = idx[m];
+        if (i < 0 || i >= N) {
+            bad = 1;
+            continue;
+        }
+        double a[3], r[3], eA, eR;
+        attraction_one(P[3 * m], P[3 * m + 1], P[3 * m + 2], rho, nx, ny, nz, lo, hi, eps, a, &eA);
+        repulsion_at(K, N, i, P[3 * m], P[3 * m + 1], P[3 * m + 2], eps, r, &eR);
+        ea[m] = eA;
+        er[m] = eR;
+    }
+    return bad ? ORACLE_EINVAL : ORACLE_OK;
 }
 
 /* Energy F = F^a - F^r (eqs. global_minimization, attraction_term,

@@ -331,3 +331,44 @@ def test_regularised_tends_to_plain_norm():
     # and eps changes the result visibly when it is not small
     A2, _, _ = oracle.forces(p.K, p.grid, eps=0.05)
     assert np.abs(A2 - A0).max() > 1e-3
+
+
+def test_energy_terms_pins():
+    """energy_terms (the terms of F that contain one sample, with the sample
+    moved): closed form for N = 2 and one density point; at the samples' own
+    positions the per-target sums of forces(); summed over the samples, F^a
+    and twice F^r (eq. global_minimization); its central differences times N
+    equal G (the repulsion's double sum counts each pair twice, a plausible
+    factor-2 mistake)."""
+    grid = one_cell(0.1, 0.3)
+    K = np.array([[0.3, -0.1, 0.2], [-0.2, 0.25, 0.0]])
+    p = np.array([[0.05, 0.1, -0.3]])
+    ea, er = oracle.energy_terms(K, grid, [0], p)
+    assert ea[0] == pytest.approx(np.linalg.norm(p[0] - 0.2), abs=1e-15)
+    assert er[0] == pytest.approx(np.linalg.norm(p[0] - K[1]), abs=1e-15)
+
+    rng = np.random.default_rng(31)
+    K = rng.uniform(-0.5, 0.5, size=(300, 3))
+    grid = random_grid((5, 7, 6), 32)
+    idx = np.arange(300)
+    ea, er = oracle.energy_terms(K, grid, idx, K)
+    _, _, _, ea0, er0 = oracle.forces(K, grid, energies=True)
+    np.testing.assert_array_equal(ea, ea0)
+    np.testing.assert_array_equal(er, er0)
+    _, Fa, Fr = oracle.energy(K, grid)
+    assert ea.sum() / 300 == pytest.approx(Fa, rel=1e-14)
+    assert er.sum() / (2 * 300 ** 2) == pytest.approx(Fr, rel=1e-14)
+
+    N, h = 300, 1e-5
+    _, _, G = oracle.forces(K, grid)
+    tgt = np.array([3, 77, 150, 299])
+    for c in range(3):
+        pp, pm = K[tgt].copy(), K[tgt].copy()
+        pp[:, c] += h
+        pm[:, c] -= h
+        eap, erp = oracle.energy_terms(K, grid, tgt, pp)
+        eam, erm = oracle.energy_terms(K, grid, tgt, pm)
+        fd = ((eap / N - erp / N ** 2) - (eam / N - erm / N ** 2)) / (2 * h) * N
+        np.testing.assert_allclose(fd, G[tgt, c], rtol=0, atol=1e-7)
+    with pytest.raises(ValueError):
+        oracle.energy_terms(K, grid, [300], K[:1])
