@@ -4,7 +4,14 @@ One step = one projected-gradient iteration of full-3D SPARKLING over the
 whole pattern (eq. proj_grad_descent / Algorithm 1 inner loop): pack, direct
 attraction sum over the density grid, direct repulsion sum, combine, and the
 per-shot projection with the gradient step fused in -- all through the C-ABI
-entry point sparkling_step.
+entry point sparkling_step_host, which copies the pattern and the density in
+from pinned host memory, steps, and copies the pattern back.
+
+Every warm-up and timed step is one such call.  In the timed steps the
+library brackets the device work of the step (after the input copies, before
+the output copy) with CUDA events on the launch stream: pairs / that time is
+`value` (inputs resident in HBM); pairs / the wall time of the whole call is
+`e2e` (host copies included).
 
 Metric: pair interactions per second, pairs = N*P + N*(N-1) per step
 (directed attraction pairs with the P density points plus directed
@@ -14,7 +21,8 @@ Default workload: 4096 shots x 2560 samples = 10,485,760 samples, density
 grid 256^3 = 16,777,216 points (the ~1e7-sample configuration).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload hr|diff|medium|small|tiny] [--acc kahan|fp64]
+                  [--workload hr|diff|medium|small|tiny|batched]
+                  [--acc kahan|fp64|fp64pair] [--projection fp64|mixed]
 
 Under torchrun (N > 1) every rank runs an independent problem instance of
 the same size (its own seed) on its own GPU: the trajectories are
@@ -54,7 +62,14 @@ def parse_args(argv=None):
     ap.add_argument("--path", choices=("kernels", "engine"), default="kernels",
                     help="single-trajectory step through sparkling_step (separate pair kernels) "
                          "or the persistent engine (sparkling_step_batched with B = 1)")
-    ap.add_argument("--acc", choices=("kahan", "fp64"), default="kahan")
+    ap.add_argument("--acc", choices=("kahan", "fp64", "fp64pair"), default="kahan",
+                    help="per-target accumulation: compensated FP32 folds, FP64 folds, or the "
+                         "plain FP64-accumulate form (every attraction pair term added in FP64)")
+    ap.add_argument("--projection", choices=("fp64", "mixed"), default="fp64",
+                    help="projection arithmetic: FP64 duals (default) or the opt-in mixed form")
+    ap.add_argument("--shot-stride", type=int, default=1,
+                    help="keep every S-th shot of the workload (same density): a smaller launch "
+                         "of the same kernels, e.g. for a profiler capture")
     ap.add_argument("--attraction", choices=("direct", "field"), default="direct",
                     help="direct sum (exact) or the interpolated node field of the density "
                          "(fast, approximate; the step's pairs are then counted as equivalent "
@@ -72,14 +87,15 @@ def parse_args(argv=None):
                     help="pin the attraction's tile shape (0/1/2: 128/256/512 threads; "
                          "-1: autotuned)")
     ap.add_argument("--shape-repulsion", type=int, default=-1,
-                    help="pin the symmetric repulsion's tile shape (0: 2 sources per lane, "
-                         "targets paired; 1: 4 sources, targets paired; 2: 2 sources, sources "
-                         "paired; -1: autotuned)")
+                    help="pin the symmetric repulsion's tile shape (256 threads: 0: 2 sources "
+                         "per lane, targets paired; 1: 4 sources, targets paired; 2: 2 sources, "
+                         "sources paired; 128 threads: 3: 8 targets and 2 sources per lane, "
+                         "sources paired; -1: autotuned)")
     ap.add_argument("--clock-log", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: the temp dir)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target duration of the oracle sample")
     ap.add_argument("--crossover", action="store_true",
                     help="instead of the step: time the exact (symmetric) and the mesh repulsion "
@@ -132,9 +148,16 @@ def barrier():
 
 # --- workload -----------------------------------------------------------------
 
-def load_problem(name: str, seed: int):
+def load_problem(name: str, seed: int, shot_stride: int = 1):
     import inputs
-    return inputs.make_problem(name, seed=seed)
+    p = inputs.make_problem(name, seed=seed)
+    if shot_stride > 1:
+        Nc = (p.Nc + shot_stride - 1) // shot_stride
+        p.K = p.K.reshape(p.Nc, p.Ns, 3)[::shot_stride].reshape(-1, 3).copy()
+        p.Nc = Nc
+        p.recipe += f"; every {shot_stride}th shot ({Nc} shots)"
+        p.eta = 1.0 / p.N if p.eta else p.eta
+    return p
 
 
 def pairs_per_step(N: int, P: int) -> int:
@@ -218,31 +241,73 @@ def measure_probe():
 
 
 
+# --- DRAM traffic of the attraction launch (from a committed ncu summary) ------
+
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "attraction_hr_traffic.md")
+ATTRACTION_SOURCES = ("pair_dev.cuh", "pairs.cu", "ptx.cuh", "kernels.h")
+
+
+def attraction_source_sha() -> str:
+    """SHA-256 (16 hex digits) of the attraction kernel's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ATTRACTION_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_02991_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def attraction_traffic(prob, args):
+    """DRAM bytes per attraction launch of this workload, from the ncu
+    summary's linear fit in the number of targets (captured on launches of
+    the same density with fewer shots); None unless the summary exists, was
+    taken on the current kernel source and covers this workload's density."""
+    import re
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic-fit:\s*kernel_sha=(\w+)\s+density=(\d+)\s+"
+                  r"bytes_const=([0-9.eE+]+)\s+bytes_per_target=([0-9.eE+]+)", text)
+    if not m or m.group(1) != attraction_source_sha() or args.acc != "kahan":
+        return None
+    if int(m.group(2)) != int(prob.grid.rho.size):
+        return None
+    b = float(m.group(3)) + float(m.group(4)) * prob.N
+    return {"bytes_per_launch": b,
+            "basis": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of launches with the same "
+                     f"density and fewer shots, fitted linearly in the targets "
+                     f"({os.path.relpath(TRAFFIC_PROFILE, ROOT)}, kernel source {m.group(1)})"}
+
+
 # --- oracle timing (the CPU baseline and the reference arm) -------------------
 
-def oracle_sample(prob, seconds: float, seed: int = 1):
-    """Time the FP64 oracle on a bounded sample of targets of the workload;
-    returns (pairs/s, description, threads)."""
+def oracle_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def oracle_sample(prob, seconds: float, seed: int = 1, K64=None):
+    """Time the FP64 oracle on a bounded sample of targets of the workload:
+    first 4 targets per core (every core busy), then, if that took less than
+    `seconds`, a sample scaled to take about `seconds`.  Returns
+    (pairs/s, description, threads)."""
     import numpy as np
     import oracle
-    K = prob.K.astype(np.float64)
+    K = prob.K.astype(np.float64) if K64 is None else K64
     N, P = K.shape[0], int(np.prod(prob.grid.n))
     rng = np.random.default_rng(seed)
     per_target = P + N - 1
-    m = 2
-    while True:
+    threads = oracle_threads()
+    m = min(N, 4 * threads)
+    for attempt in range(2):
         idx = rng.choice(N, size=m, replace=False)
         t0 = time.perf_counter()
         oracle.forces(K, prob.grid, targets=idx)
         dt = time.perf_counter() - t0
-        if dt >= seconds or m >= N:
+        if attempt or dt >= 0.8 * seconds or m >= N:
             break
-        if dt > 0.25:
-            m = min(N, max(m + 1, int(m * seconds / dt * 1.05)))
-        else:
-            m = min(N, m * 4)
+        m = min(N, max(m, int(m * seconds / max(dt, 1e-6))))
     pairs = m * per_target
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = (f"{m} random targets of the {prob.name} workload, each against all "
             f"{P} density points and {N - 1} samples ({pairs:.3e} FP64 pairs, {dt:.1f} s)")
     return pairs / dt, desc, threads
@@ -260,15 +325,20 @@ def run_reference(args):
         P = int(prob.grid.rho.size)
         pairs_step = sum(pairs_per_step(q.N, int(q.grid.rho.size)) for q in probs)
     else:
-        prob = load_problem(args.workload, 0)
+        prob = load_problem(args.workload, 0, args.shot_stride)
         N, P = prob.N, int(prob.grid.rho.size)
         pairs_step = pairs_per_step(N, P)
+    import numpy as np
+    K64 = prob.K.astype(np.float64)
     vals = []
     desc = threads = None
+    # every sample keeps every core busy (4 targets per core at least); the
+    # whole run stays at about 2 * cpu_seconds plus the warm-up samples
     for _ in range(args.warmup):
-        oracle_sample(prob, min(args.cpu_seconds, 3.0) / 3)
-    for _ in range(args.steps):
-        v, desc, threads = oracle_sample(prob, args.cpu_seconds / max(args.steps, 1))
+        oracle_sample(prob, 0.0, K64=K64)
+    for k in range(args.steps):
+        v, desc, threads = oracle_sample(prob, 2 * args.cpu_seconds / max(args.steps, 1),
+                                         seed=1 + k, K64=K64)
         vals.append(v)
     value = statistics.median(vals)
     unit = "pairs/s"
@@ -291,26 +361,35 @@ def run_reference(args):
 # --- our implementation --------------------------------------------------------
 
 class Workload:
-    """Device state and the step call of one benchmark workload."""
+    """Device state and the step calls of one benchmark workload."""
 
     def __init__(self, sp, args, dev, seed):
+        import numpy as np
         import torch
         self.sp, self.args, self.dev = sp, args, dev
-        self.acc = sp.ACC_KAHAN32 if args.acc == "kahan" else sp.ACC_FP64
+        self.acc = {"kahan": sp.ACC_KAHAN32, "fp64": sp.ACC_FP64,
+                    "fp64pair": sp.ACC_FP64_PAIR}[args.acc]
         if args.workload == "batched":
             import inputs
             self.probs = inputs.make_batched(seed=seed)
         else:
-            self.probs = [load_problem(args.workload, seed)]
+            self.probs = [load_problem(args.workload, seed, args.shot_stride)]
         self.batched = args.workload == "batched" or args.path == "engine"
         self.off = [0]
         for p in self.probs:
             self.off.append(self.off[-1] + p.N)
         self.Ns = self.probs[0].Ns
-        self.K = torch.from_numpy(__import__("numpy").concatenate([p.K for p in self.probs])).to(dev)
-        self.rhos = [torch.from_numpy(p.grid.rho).to(dev) for p in self.probs]
+        K = np.ascontiguousarray(np.concatenate([p.K for p in self.probs]))
+        # pinned host copies: the inputs every step copies in, and the result
+        # it copies back (the pattern evolves step by step, as in the method)
+        self.Kh = torch.from_numpy(K).pin_memory()
+        self.rhoh = [torch.from_numpy(p.grid.rho).pin_memory() for p in self.probs]
+        self.K = self.Kh.to(dev)
+        self.rhos = [r.to(dev) for r in self.rhoh]
         self.grids = [sp.make_grid(r, p.grid.lo, p.grid.hi, p.grid.n)
                       for r, p in zip(self.rhos, self.probs)]
+        self.hgrid = sp.make_grid(self.rhoh[0], self.probs[0].grid.lo, self.probs[0].grid.hi,
+                                  self.probs[0].grid.n)
         self.projs = [sp.make_proj(p.proj.alpha, p.proj.beta, p.proj.box, p.proj.n_iter,
                                    p.proj.pin_index, p.proj.pin) for p in self.probs]
         self.etas = [p.eta for p in self.probs]
@@ -322,8 +401,11 @@ class Workload:
                          f"(total {self.N}), 64^3 Gaussian densities")
         else:
             self.desc = f"{args.workload}: {p0.recipe}"
+        self.kbytes = int(self.Kh.numel() * self.Kh.element_size())
+        self.rhobytes = int(sum(r.numel() * r.element_size() for r in self.rhoh))
 
-    def step(self):
+    def step_device(self):
+        """One step on device-resident K (asynchronous)."""
         sp = self.sp
         if self.batched:
             sp.sparkling_step_batched(self.ctx, self.K, self.off, self.Ns, self.grids, self.etas,
@@ -333,9 +415,32 @@ class Workload:
             sp.sparkling_step(self.ctx, self.K, p.Nc, p.Ns, self.grids[0], p.eta, self.projs[0],
                               self.acc)
 
+    def step_host(self, stream):
+        """One step from and to the pinned host buffers (blocking).  Returns
+        the CUDA events around the device work when they are recorded here
+        (the batched step), else None (the library's STEP scope times it)."""
+        import torch
+        sp = self.sp
+        if not self.batched:
+            p = self.probs[0]
+            sp.sparkling_step_host(self.ctx, self.Kh, p.Nc, p.Ns, self.hgrid, self.rhoh[0],
+                                   p.eta, self.projs[0], self.acc)
+            return None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        self.K.copy_(self.Kh, non_blocking=True)
+        for r, rh in zip(self.rhos, self.rhoh):
+            r.copy_(rh, non_blocking=True)
+        e0.record(stream)
+        self.step_device()
+        e1.record(stream)
+        self.Kh.copy_(self.K, non_blocking=True)
+        stream.synchronize()
+        sp.sparkling_status(self.ctx)
+        return e0, e1
+
 
 def run_ours(args):
-    import numpy as np
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -355,16 +460,19 @@ def run_ours(args):
         sp.sparkling_set_shape(ctx, "attraction", args.shape_attraction)
     if args.shape_repulsion >= 0:
         sp.sparkling_set_shape(ctx, "repulsion", args.shape_repulsion)
+    sp.sparkling_set_projection(ctx, sp.PROJECTION_MIXED if args.projection == "mixed"
+                                else sp.PROJECTION_FP64)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     field_build_ms = None
     mesh_build_ms = None
+    fast = args.attraction == "field" or args.repulsion == "mesh"
     if args.repulsion == "mesh":
         sp.sparkling_set_repulsion(ctx, sp.REPULSION_MESH,
                                    sp.make_mesh(args.mesh_cells, args.mesh_sigma, args.mesh_rc))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        w.step()                                  # builds the kernel spectra (blocking)
+        w.step_device()                           # builds the kernel spectra (blocking)
         sp.sparkling_status(ctx)
         mesh_build_ms = (time.perf_counter() - t0) * 1e3
     if args.attraction == "field":
@@ -374,8 +482,31 @@ def run_ours(args):
         sp.sparkling_attraction_field(ctx, w.grids[0])      # blocking
         field_build_ms = (time.perf_counter() - t0) * 1e3
 
+    # The fast modes keep the density's node field across steps, which a
+    # host-buffer step (new density every call) would rebuild: they time the
+    # device-resident step, and their e2e leg (optional) is a separate loop.
+    # The exact paths run one loop of host-buffer steps for both numbers.
+    one_loop = not fast
+
+    def one_step(timed):
+        flush.zero_()                        # evict L2 between steps (outside the timing)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        if one_loop:
+            ev = w.step_host(stream)
+        else:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            w.step_device()
+            e1.record(stream)
+            e1.synchronize()
+            ev = (e0, e1)
+        t1 = time.perf_counter()
+        return (t1 - t0), ev
+
     for _ in range(args.warmup):
-        w.step()
+        one_step(False)
     sp.sparkling_status(ctx)
     torch.cuda.synchronize(dev)
 
@@ -386,16 +517,12 @@ def run_ours(args):
     clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
-    step_ms = []
+    wall_s, evs = [], []
     for _ in range(args.steps):
-        flush.zero_()                        # evict L2 between timed steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        w.step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        dt, ev = one_step(True)
+        wall_s.append(dt)
+        if ev is not None:
+            evs.append(ev)
     torch.cuda.synchronize(dev)
     barrier()
     clk = clocks.stop()
@@ -404,10 +531,43 @@ def run_ours(args):
     ktimes = sp.sparkling_kernel_times(ctx, reset=True)
     sp.sparkling_set_timing(ctx, False)
 
+    # device time of the timed steps: the library's STEP scopes (single
+    # trajectory) or the events around each batched step
+    if evs:
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+    else:
+        ms, n = ktimes["step"]
+        if n != args.steps:
+            raise RuntimeError(f"expected {args.steps} timed step scopes, got {n}")
+        step_ms = [ms / n] * n
     local_ms = sum(step_ms)
     total_ms = reduce_max(local_ms, dev)
     pairs_all = reduce_sum(float(w.pairs * args.steps), dev)
     value = pairs_all / (total_ms * 1e-3)
+
+    e2e = None
+    if one_loop:
+        e2e_s = reduce_max(sum(wall_s), dev)
+        e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s",
+               "h2d_bytes_per_step": w.kbytes + w.rhobytes, "d2h_bytes_per_step": w.kbytes,
+               "seconds_per_step": e2e_s / args.steps,
+               "note": "the same timed steps: each a sparkling_step_host call (pinned K and "
+                       "density copied in, K copied back), wall clock around the call"}
+    elif not args.no_e2e:
+        # fast modes: the host-buffer step rebuilds the density's node field
+        # every call (a new density arrives with each call)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            w.step_host(stream)
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = reduce_max(t1 - t0, dev)
+        e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s",
+               "h2d_bytes_per_step": w.kbytes + w.rhobytes, "d2h_bytes_per_step": w.kbytes,
+               "seconds_per_step": e2e_s / args.steps,
+               "note": "separate loop of sparkling_step_host calls"}
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
@@ -417,15 +577,12 @@ def run_ours(args):
         pass
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     probe = measure_probe() if rank == 0 else {}
-    rsq = probe.get("rsqrt")
+    rsq = probe.get("rsqrt") if probe else None
     rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
     peak = sms * rate * max_mhz * 1e6
     if w.batched:
         # one engine launch runs every pair of the step: N_b*P_b + N_b*(N_b-1)
         kname, kpairs = "engine", w.pairs
-    elif args.repulsion == "mesh" and args.attraction == "direct":
-        p0 = w.probs[0]
-        kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
     elif args.attraction == "field" and args.repulsion == "direct":
         # the attraction is an interpolation; the symmetric repulsion takes
         # one reciprocal square root per unordered pair
@@ -437,56 +594,32 @@ def run_ours(args):
         kname, kpairs = "attraction", p0.N * int(p0.grid.rho.size)
     k_ms, k_n = ktimes[kname] if kname else (0.0, 0)
     achieved = kpairs / (k_ms / k_n * 1e-3) if k_n else None
+    traffic = None
+    if kname == "attraction" and not w.batched:
+        traffic = attraction_traffic(w.probs[0], args)
     roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak / 1e9, "unit": "Gpair/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic["bytes_per_launch"] if traffic else None,
             "kernel": kname,
             "peak_basis": f"{sms} SMs x {rate:g} MUFU.RSQ/clk/SM x {max_mhz:.0f} MHz max SM clock "
                           f"(one reciprocal square root per pair; probe measured "
                           f"{rsq if rsq else 'n/a'} RSQ/clk/SM)"}
+    if traffic:
+        roof["traffic_basis"] = traffic["basis"]
     if clk and achieved:
         roof["frac_at_measured_clock"] = achieved / (sms * rate * clk["sm_mhz"] * 1e6)
-    tot_k = max(sum(v[0] for v in ktimes.values()), 1e-9)
+    tot_k = max(sum(v[0] for k, v in ktimes.items() if k != "step"), 1e-9)
     kernels = {k: {"ms_total": round(ms, 3), "launches": n, "share": round(ms / tot_k, 4)}
-               for k, (ms, n) in ktimes.items() if n}
-    if not w.batched and ktimes["repulsion"][1]:
+               for k, (ms, n) in ktimes.items() if n and k != "step"}
+    if not w.batched and ktimes["repulsion"][1] and args.repulsion == "direct":
         rep_ms, rep_n = ktimes["repulsion"]
-        kernels["repulsion"]["gpair_per_s"] = w.N * (w.N - 1) / (rep_ms / rep_n * 1e-3) / 1e9
-
-    e2e = None
-    if not args.no_e2e and not w.batched:
-        p = w.probs[0]
-        Kh = torch.from_numpy(p.K).pin_memory()
-        rhoh = torch.from_numpy(p.grid.rho).pin_memory()
-        hgrid = sp.make_grid(rhoh, p.grid.lo, p.grid.hi, p.grid.n)
-        barrier()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            sp.sparkling_step_host(ctx, Kh, p.Nc, p.Ns, hgrid, rhoh, p.eta, w.projs[0], w.acc)
-        t1 = time.perf_counter()
-        barrier()
-        e2e_s = reduce_max(t1 - t0, dev)
-        e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s",
-               "h2d_bytes_per_step": int(Kh.numel() * Kh.element_size() + rhoh.numel() * 4),
-               "d2h_bytes_per_step": int(Kh.numel() * Kh.element_size())}
-    elif not args.no_e2e:
-        # batched: pinned host copy of K in and out around every step
-        Kh = w.K.cpu().pin_memory()
-        barrier()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            w.K.copy_(Kh, non_blocking=True)
-            w.step()
-            Kh.copy_(w.K, non_blocking=True)
-            torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
-        barrier()
-        e2e_s = reduce_max(t1 - t0, dev)
-        nb = int(Kh.numel() * Kh.element_size())
-        e2e = {"value": pairs_all / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb, "note": "densities resident on the device"}
+        per = rep_ms / rep_n * 1e-3
+        kernels["repulsion"]["gpair_per_s"] = w.N * (w.N - 1) / per / 1e9
+        # FP32-pipe bound of the symmetric kernel: 12 FP32 lane operations per
+        # unordered pair on 128 lanes per SM per clock
+        kernels["repulsion"]["frac_of_fp32_bound"] = (
+            w.N * (w.N - 1) / 2 / per / (sms * 128.0 / 12.0 * max_mhz * 1e6))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -495,18 +628,23 @@ def run_ours(args):
 
     if rank == 0:
         p0 = w.probs[0]
+        proj_form = ("mixed FP32/FP64 projection" if args.projection == "mixed"
+                     else "FP64 projection (duals, primal, step)")
+        acc_form = {"kahan": "compensated-f32 per-target sums",
+                    "fp64": "f64 per-target sums of f32 row sums",
+                    "fp64pair": "every attraction pair term added in f64"}[args.acc]
         out = {
             "metric": "pair_interactions_per_s", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32 pairs, " + ("compensated-f32" if w.acc == 0 else "f64")
-                     + " per-target sums, f64 projection",
+            "dtype": f"f32 pairs, {acc_form}, {proj_form}",
             "data": "synthetic",
             "config": {"workload": w.desc, "N": w.N, "P": int(p0.grid.rho.size),
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
                        "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
-                       "l2": "flushed (512 MB write) between timed steps", "acc": args.acc,
+                       "l2": "flushed (512 MB write) before every step", "acc": args.acc,
+                       "projection": args.projection,
                        "attraction": args.attraction, "repulsion": args.repulsion,
                        "shapes": ("autotuned" if args.shape_attraction < 0
                                   and args.shape_repulsion < 0 else
@@ -515,6 +653,7 @@ def run_ours(args):
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "seconds_per_iteration": total_ms / args.steps / 1e3,
+            "step_ms": [round(v, 3) for v in step_ms],
             "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
             "alu_probe_per_sm_clk": probe or None,
         }

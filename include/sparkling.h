@@ -73,11 +73,19 @@ extern "C" {
 #define SPARKLING_F64 1
 
 /* Per-target accumulation of the FP32 pair sums.
- * KAHAN32: every grid row / source block is summed in FP32 and folded into a
- *          compensated (TwoSum) FP32 accumulator.
- * FP64:    the same FP32 partial sums are folded into FP64 accumulators. */
+ * KAHAN32:   every grid row / source block is summed in FP32 and folded into
+ *            a compensated (TwoSum) FP32 accumulator.
+ * FP64:      the same FP32 partial sums are folded into FP64 accumulators.
+ * FP64_PAIR: the plain FP64-accumulate form, kept to compare against: every
+ *            attraction pair term is converted to FP64 and added to FP64
+ *            sums one by one (GB300's FP64 pipe bounds it; about 30 times
+ *            slower).  The repulsion then folds its FP32 block sums in FP64.
+ *            Accepted by sparkling_grad, sparkling_energy,
+ *            sparkling_energy_backward, sparkling_step and the driver; the
+ *            batched step and sparkling_grad_noalloc reject it. */
 #define SPARKLING_ACC_KAHAN32 0
 #define SPARKLING_ACC_FP64 1
+#define SPARKLING_ACC_FP64_PAIR 2
 
 typedef struct sparkling_ctx sparkling_ctx;
 
@@ -121,7 +129,12 @@ typedef struct sparkling_proj {
 #define SPARKLING_KERNEL_PROJECT 4
 #define SPARKLING_KERNEL_ENGINE 5   /* a whole batched step (packs + persistent engine) */
 #define SPARKLING_KERNEL_DRIVER 6   /* up-sampling and step-size reductions of the driver */
-#define SPARKLING_KERNEL_COUNT 7
+#define SPARKLING_KERNEL_STEP 7     /* the whole device work of one sparkling_step call */
+#define SPARKLING_KERNEL_COUNT 8
+
+/* Arithmetic of the projection (sparkling_set_projection). */
+#define SPARKLING_PROJECTION_FP64 0    /* duals, primal and step in FP64 for every K dtype (default) */
+#define SPARKLING_PROJECTION_MIXED 1   /* FP32 K, fixed n_iter: FP32 iteration on s - k and the duals */
 
 /* How the attraction term is evaluated (sparkling_set_attraction). */
 #define SPARKLING_ATTRACTION_DIRECT 0   /* direct sum over the grid: O(N P) */
@@ -205,7 +218,8 @@ SPARKLING_API int sparkling_energy_backward(sparkling_ctx *ctx, const void *K, i
 
 /* Projection of each of Nc shots of Ns samples onto the constraint set
  * (Sec. II-D, Suppl. Sec. I), in place on K ([Nc*Ns][3], K_dtype), with the
- * dual FISTA iteration in FP64:
+ * dual FISTA iteration in FP64 (sparkling_set_projection: the opt-in mixed
+ * form for FP32 K):
  *   D1 s[n] = s[n+1]-s[n], D2 s[n] = s[n+2]-2s[n+1]+s[n];
  *   s(q) = pin(clip_box(k - D1^T q1 - D2^T q2)); step tau = 1/20;
  *   z = y + tau D s(y); q+ = z - P_ball(tau*alpha or tau*beta)(z) per row;
@@ -221,8 +235,11 @@ SPARKLING_API int sparkling_project(sparkling_ctx *ctx, void *K, int K_dtype, in
 /* One projected-gradient step (eq. proj_grad_descent, Algorithm 1 inner
  * loop): K <- Pi(K - eta * G(K)) in place, G = A - R as in sparkling_grad
  * (so eta = 1/N is a unit step on dF/dK).  The gradient is kept in FP64 in
- * the workspace; the step and the projection run in FP64 and the result is
- * rounded to K_dtype.  Asynchronous unless converged mode is requested. */
+ * the workspace; the step and the projection run in FP64 (unless the
+ * context chose SPARKLING_PROJECTION_MIXED) and the result is rounded to
+ * K_dtype.  With timing on, the device work of the call is also timed as one
+ * SPARKLING_KERNEL_STEP scope.  Asynchronous unless converged mode is
+ * requested. */
 SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns,
                                  const sparkling_grid *grid, int acc, double eta,
                                  const sparkling_proj *proj, void *stream);
@@ -303,8 +320,9 @@ SPARKLING_API int sparkling_status(sparkling_ctx *ctx, void *stream);
  * (SPARKLING_KERNEL_*), the total milliseconds and the number of timed
  * scopes since the last reset (one per launch, except PACK -- samples and
  * density packed together -- COMBINE in energy mode -- two reduction kernels
- * -- and ENGINE -- a whole batched step); reset != 0 clears the totals
- * afterwards. */
+ * -- ENGINE -- a whole batched step -- and STEP -- the whole device work of a
+ * sparkling_step or sparkling_step_host call, between the host copies);
+ * reset != 0 clears the totals afterwards. */
 SPARKLING_API int sparkling_set_timing(sparkling_ctx *ctx, int enable);
 SPARKLING_API int sparkling_kernel_times(sparkling_ctx *ctx, double *ms_out, int64_t *launches_out,
                                          int n, int reset);
@@ -327,10 +345,12 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
  * 1, 2 = 128, 256, 512 threads per CTA (8, 4, 2 targets per thread).
  * kernel = SPARKLING_KERNEL_REPULSION (the symmetric kernel of
  * sparkling_grad, sparkling_energy, sparkling_step and the batched step):
- * variant 0 = 2 sources per lane, targets paired in the 64-bit registers;
- * 1 = 4 sources per lane, targets paired; 2 = 2 sources per lane, the two
- * sources paired (the shape used where nothing is tuned or pinned, e.g. by
- * the batched step).  variant = -1 unpins (the next call of a new key tunes
+ * variant 0 = 256 threads per CTA (4 targets per lane), 2 sources per lane,
+ * targets paired in the 64-bit registers; 1 = 256 threads, 4 sources per
+ * lane, targets paired; 2 = 256 threads, 2 sources per lane, the two sources
+ * paired (the shape used where nothing is tuned or pinned, e.g. by the
+ * batched step); 3 = 128 threads per CTA (8 targets per lane), 2 sources
+ * paired.  variant = -1 unpins (the next call of a new key tunes
  * again when the autotuner is on).  sparkling_set_autotune(ctx, -1) unpins
  * both.  Returns SPARKLING_E_INVAL for another kernel or variant. */
 SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int variant);
@@ -351,6 +371,38 @@ SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, i
  * self pairs (i = j), as F^r does.  Returns SPARKLING_E_INVAL unless
  * 0 <= eps <= 1e3. */
 SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps);
+
+/* Arithmetic of the context's projections (sparkling_project, sparkling_step,
+ * sparkling_step_host, sparkling_step_batched, the driver).
+ *   SPARKLING_PROJECTION_FP64 (default): the dual FISTA iteration, the primal
+ *     map and the step in FP64 for every K dtype; the result is rounded to
+ *     K_dtype once.
+ *   SPARKLING_PROJECTION_MIXED: for FP32 K with a fixed n_iter, the iteration
+ *     runs in FP32 on the displacement e = s - k and the duals (D1 k, D2 k and
+ *     the box and pin offsets formed once per shot in FP64, the output
+ *     k + e in FP64); FP64 K and converged mode keep the FP64 iteration.
+ * Returns SPARKLING_E_INVAL for another mode. */
+SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode);
+
+/* Budget of the context's bounded device waits (a TMA copy's mbarrier, the
+ * batched step's wait for a trajectory's pair items), in SM clock cycles;
+ * cycles < 0 restores the default 4e9 (about 2 s).  A wait that runs past it
+ * sets the status bit that makes the call (or the next sparkling_status)
+ * return SPARKLING_E_TIMEOUT, and its kernel returns early, leaving its
+ * outputs incomplete; the context stays usable.  After a timeout a CTA still
+ * waits, with the default budget, for its own copies in flight before it
+ * exits.  A small budget is a way to exercise that path; 0 makes every wait
+ * that does not succeed at once time out.  Synchronises the device when the
+ * context is already in use.  Returns SPARKLING_E_INVAL above 2^40 cycles. */
+SPARKLING_API int sparkling_set_wait_budget(sparkling_ctx *ctx, int64_t cycles);
+
+/* Cap on the device memory the context allocates for itself (its workspace,
+ * the device copies of sparkling_step_host and the attraction field; the
+ * fast-repulsion mesh allocates outside it), in bytes; 0 (the default)
+ * removes the cap.  A call whose allocation would take the context past the
+ * cap returns SPARKLING_E_NOMEM before anything is launched and leaves the
+ * context usable.  Returns SPARKLING_E_INVAL for bytes < 0. */
+SPARKLING_API int sparkling_set_memory_limit(sparkling_ctx *ctx, int64_t bytes);
 
 /* Attraction mode of the context's sparkling_grad, sparkling_energy,
  * sparkling_energy_backward and sparkling_step calls (the batched step and

@@ -21,7 +21,7 @@ NumPy arrays.  See the C file for the definitions followed:
 * ``violation`` -- the constraint checker;
 * ``step``    -- one projected-gradient step (eq. proj_grad_descent).
 
-Fast repulsion (particle-mesh split, see ``p3m.py`` for the mesh part):
+Fast repulsion (the exact particle-mesh split of the kernel):
 
 * ``repulsion_split`` -- exact short-range (erfc, cut at rc) and long-range
   (erf) parts of the repulsion and of its distance sums.

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libsparkling.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOTCONV, E_IO, E_RANGE = range(9)
 F32, F64 = 0, 1
-ACC_KAHAN32, ACC_FP64 = 0, 1
-KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine", "driver")
+ACC_KAHAN32, ACC_FP64, ACC_FP64_PAIR = 0, 1, 2
+KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine", "driver", "step")
+PROJECTION_FP64, PROJECTION_MIXED = 0, 1
 BATCH_GRAPH = 1
 ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
 REPULSION_DIRECT, REPULSION_MESH = 0, 1
@@ -32,7 +33,8 @@ ABI_SYMBOLS = (
     "sparkling_step_batched", "sparkling_set_autotune", "sparkling_tuning_report",
     "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
     "sparkling_upsample", "sparkling_optimize", "sparkling_multires", "sparkling_set_repulsion",
-    "sparkling_set_shape",
+    "sparkling_set_shape", "sparkling_set_projection", "sparkling_set_wait_budget",
+    "sparkling_set_memory_limit",
 )
 
 
@@ -124,6 +126,9 @@ def lib() -> ctypes.CDLL:
             "sparkling_set_attraction": ([p, i], i),
             "sparkling_attraction_field": ([p, p, p], i),
             "sparkling_set_regularisation": ([p, ctypes.c_double], i),
+            "sparkling_set_projection": ([p, i], i),
+            "sparkling_set_wait_budget": ([p, i64], i),
+            "sparkling_set_memory_limit": ([p, i64], i),
             "sparkling_set_repulsion": ([p, i, p], i),
             "sparkling_upsample": ([p, p, p, i, i64, i64, p], i),
             "sparkling_optimize": ([p, p, i, i64, i64, p, p, i, p, p, p], i),
@@ -373,8 +378,10 @@ def sparkling_set_autotune(ctx: Context, enable: int = 1) -> None:
 
 def sparkling_set_shape(ctx: Context, kernel: str, variant: int) -> None:
     """Pin the tile shape of "attraction" (0/1/2: 128/256/512 threads) or of
-    the symmetric "repulsion" (0: 2 sources per lane, targets paired; 1: 4
-    sources, targets paired; 2: 2 sources, sources paired); -1 unpins."""
+    the symmetric "repulsion" (0: 256 threads, 2 sources per lane, targets
+    paired; 1: 256 threads, 4 sources, targets paired; 2: 256 threads, 2
+    sources, sources paired; 3: 128 threads, 8 targets per lane, 2 sources,
+    sources paired); -1 unpins."""
     _check(ctx, lib().sparkling_set_shape(ctx.handle, KERNEL_NAMES.index(kernel), int(variant)))
 
 
@@ -388,6 +395,23 @@ def sparkling_set_attraction(ctx: Context, mode: int) -> None:
     """ATTRACTION_DIRECT (direct sum, default) or ATTRACTION_FIELD
     (interpolated node field of the density)."""
     _check(ctx, lib().sparkling_set_attraction(ctx.handle, int(mode)))
+
+
+def sparkling_set_projection(ctx: Context, mode: int) -> None:
+    """PROJECTION_FP64 (default: FP64 iteration for every K dtype) or
+    PROJECTION_MIXED (FP32 K: FP32 iteration on the displacement)."""
+    _check(ctx, lib().sparkling_set_projection(ctx.handle, int(mode)))
+
+
+def sparkling_set_wait_budget(ctx: Context, cycles: int) -> None:
+    """Budget of the context's bounded device waits in SM clock cycles
+    (negative: the default, about 2 s)."""
+    _check(ctx, lib().sparkling_set_wait_budget(ctx.handle, int(cycles)))
+
+
+def sparkling_set_memory_limit(ctx: Context, nbytes: int) -> None:
+    """Cap on the context's own device allocations (0: none)."""
+    _check(ctx, lib().sparkling_set_memory_limit(ctx.handle, int(nbytes)))
 
 
 def sparkling_set_regularisation(ctx: Context, eps: float) -> None:

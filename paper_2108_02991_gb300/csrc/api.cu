@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -26,7 +27,10 @@ struct sparkling_ctx {
     int device = 0;
     bool inited = false;
     int sms = 0;
-    int *d_status = nullptr;    // device status word
+    int *d_status = nullptr;    // device control block (DevCtl): status word, wait budget
+    long long wait_cycles = kWaitCycles;   // budget of the kernels' bounded waits
+    size_t mem_limit = 0;       // cap on the context's device allocations (0: none)
+    int proj_mode = SPARKLING_PROJECTION_FP64;
     double *d_small = nullptr;  // [0..1] energy, [2..5] violation bits, [6] notconv (int)
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -43,8 +47,9 @@ struct sparkling_ctx {
     double ms[SPARKLING_KERNEL_COUNT] = {};
     int64_t nlaunch[SPARKLING_KERNEL_COUNT] = {};
     int64_t launches = 0;
-    // occupancy cache [acc][energy][variant]
-    int occ_attr[2][2][kAttrVariants] = {};
+    // occupancy cache [acc][energy][variant] (the directed repulsion has no
+    // plain FP64-accumulate form: it runs with the FP64 fold, rep_acc())
+    int occ_attr[3][2][kAttrVariants] = {};
     int occ_rep[2][2][kRepVariants] = {};
     bool occ_done = false;
     // autotuner: tile shape per (acc, padded row length) for the attraction
@@ -80,6 +85,7 @@ struct sparkling_ctx {
         std::vector<const void *> graph_key;
         int graph_variant = -1;
         float graph_eps2 = -1.f;          // eps^2 baked into the captured launch
+        int graph_proj = -1;              // projection mode baked into the captured launch
         int eager_calls = 0;
     } batch;
     cudaStream_t cap_stream = nullptr;  // private stream the batched step is captured on
@@ -106,6 +112,11 @@ struct sparkling_ctx {
 namespace {
 
 thread_local std::string g_err = "no error";
+
+// Accumulation of the directed repulsion for a requested mode: the plain
+// FP64-accumulate form applies to the attraction; the repulsion then folds
+// its FP32 block sums in FP64.
+int rep_acc(int acc) { return acc > SPARKLING_ACC_FP64 ? SPARKLING_ACC_FP64 : acc; }
 
 // eps^2 as the pair kernels add it to r^2 (never below the zero-distance guard)
 float eps2_of(const sparkling_ctx *ctx)
@@ -149,15 +160,18 @@ int lazy_init(sparkling_ctx *ctx)
         return fail(ctx, SPARKLING_E_CUDA, "device %d not present (%d devices)", ctx->device, n);
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    CK(cudaMalloc(&ctx->d_status, sizeof(int)));
-    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    CK(cudaMalloc(&ctx->d_status, sizeof(DevCtl)));
+    DevCtl ctl{};
+    ctl.wait_cycles = ctx->wait_cycles;
+    CK(cudaMemcpy(ctx->d_status, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_small, 8 * sizeof(double)));
     CK(cudaMemset(ctx->d_small, 0, 8 * sizeof(double)));
     ctx->inited = true;
     return SPARKLING_OK;
 }
 
-// Device (or managed) memory the current device can dereference.
+// Device memory of the current device (the context's: lazy_init makes it
+// current), or managed memory.
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -166,7 +180,13 @@ bool is_device_ptr(const void *p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -182,16 +202,34 @@ struct Carve {
     }
 };
 
+// Device bytes the context holds besides the buffer being replaced.
+size_t held_bytes(const sparkling_ctx *ctx) { return ctx->ws_bytes + ctx->h_K_bytes + ctx->h_rho_bytes + ctx->field_cap; }
+
+// The context's allocation cap (sparkling_set_memory_limit): a request that
+// would take the context's device memory past it fails before any launch.
+int check_limit(sparkling_ctx *ctx, size_t other, size_t bytes, const char *what)
+{
+    if (ctx->mem_limit && other + bytes > ctx->mem_limit)
+        return fail(ctx, SPARKLING_E_NOMEM,
+                    "%s of %zu bytes would take the context to %zu bytes, over its limit of %zu",
+                    what, bytes, other + bytes, ctx->mem_limit);
+    return SPARKLING_OK;
+}
+
 int ensure_ws(sparkling_ctx *ctx, size_t bytes)
 {
     if (bytes <= ctx->ws_bytes) return SPARKLING_OK;
+    const size_t other = held_bytes(ctx) - ctx->ws_bytes;
+    int s;
+    if ((s = check_limit(ctx, other, bytes, "workspace"))) return s;
     // Growth is rare (first call of a larger problem): synchronise so that no
     // queued kernel still uses the old buffer, then reallocate with headroom.
     CK(cudaDeviceSynchronize());
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
-    const size_t want = align_up(bytes + bytes / 8, 1 << 20);
+    size_t want = align_up(bytes + bytes / 8, 1 << 20);
+    if (ctx->mem_limit && other + want > ctx->mem_limit) want = bytes;
     cudaError_t e = cudaMalloc(&ctx->ws, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -239,6 +277,37 @@ struct LaunchScope {
             cudaEventRecord(b, st);
             ctx->pending.push_back({kind, a, b});
         }
+    }
+};
+
+// The device work of one whole step (sparkling_step), timed as one scope of
+// kind SPARKLING_KERNEL_STEP when timing is on.  Launches inside it are
+// counted by their own scopes.
+struct StepScope {
+    sparkling_ctx *ctx;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StepScope(sparkling_ctx *c, cudaStream_t s) : ctx(c), st(s)
+    {
+        if (ctx->timing) {
+            a = get_event(ctx);
+            b = get_event(ctx);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    void done()
+    {
+        ctx->nlaunch[SPARKLING_KERNEL_STEP] += 1;
+        if (a && b) {
+            cudaEventRecord(b, st);
+            ctx->pending.push_back({SPARKLING_KERNEL_STEP, a, b});
+            a = b = nullptr;
+        }
+    }
+    ~StepScope()
+    {   // an early return: the events go back to the pool unrecorded
+        if (a) ctx->pool.push_back(a);
+        if (b) ctx->pool.push_back(b);
     }
 };
 
@@ -301,12 +370,13 @@ struct PairPlan {
 int ensure_occupancy(sparkling_ctx *ctx)
 {
     if (ctx->occ_done) return SPARKLING_OK;
-    for (int acc = 0; acc < 2; ++acc)
+    for (int acc = 0; acc < 3; ++acc)
         for (int e = 0; e < 2; ++e) {
             for (int v = 0; v < kAttrVariants; ++v)
                 ctx->occ_attr[acc][e][v] = attraction_ctas_per_sm(acc, e != 0, v);
-            for (int v = 0; v < kRepVariants; ++v)
-                ctx->occ_rep[acc][e][v] = repulsion_ctas_per_sm(acc, e != 0, v);
+            if (acc < 2)
+                for (int v = 0; v < kRepVariants; ++v)
+                    ctx->occ_rep[acc][e][v] = repulsion_ctas_per_sm(acc, e != 0, v);
         }
     for (int e = 0; e < 2; ++e)
         for (int v = 0; v < kSymVariants; ++v)
@@ -315,9 +385,9 @@ int ensure_occupancy(sparkling_ctx *ctx)
     for (int e = 0; e < 2; ++e)
         for (int v = 0; v < kSymVariants; ++v)
             if (ctx->occ_sym[e][v] < 1) ctx->rep_symmetric = false;
-    for (int acc = 0; acc < 2; ++acc)
+    for (int acc = 0; acc < 3; ++acc)
         for (int e = 0; e < 2; ++e)
-            if (ctx->occ_attr[acc][e][kAttrDefault] < 1 || ctx->occ_rep[acc][e][kRepDefault] < 1)
+            if (ctx->occ_attr[acc][e][kAttrDefault] < 1 || ctx->occ_rep[rep_acc(acc)][e][kRepDefault] < 1)
                 return fail(ctx, SPARKLING_E_CUDA, "pair kernels cannot be resident (occupancy 0)");
     ctx->occ_done = true;
     return SPARKLING_OK;
@@ -342,7 +412,7 @@ void set_splits(sparkling_ctx *ctx, PairPlan &P, int acc, bool energy, int va, i
     P.va = va;
     P.vr = vr;
     P.spa = make_split(P.tiles, rows, (int64_t)ctx->sms * ctx->occ_attr[acc][e][va]);
-    P.spr = make_split(P.tiles, nblocks, (int64_t)ctx->sms * ctx->occ_rep[acc][e][vr]);
+    P.spr = make_split(P.tiles, nblocks, (int64_t)ctx->sms * ctx->occ_rep[rep_acc(acc)][e][vr]);
 }
 
 int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, bool energy,
@@ -354,7 +424,7 @@ int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, 
     P.nx = g->n[0]; P.ny = g->n[1]; P.nz = g->n[2];
     P.gxp = (P.nx + 3) / 4 * 4;
     P.tiles = (N + kTile - 1) / kTile;
-    const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[acc];
+    const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[rep_acc(acc)];
     set_splits(ctx, P, acc, energy, va < 0 ? kAttrDefault : va, vr < 0 ? kRepDefault : vr);
     // Partial buffers big enough for every tile shape and for the tuning
     // trials (which run on a prefix of the tiles with one wave of CTAs).
@@ -363,7 +433,7 @@ int plan_pairs(sparkling_ctx *ctx, int64_t N, const sparkling_grid *g, int acc, 
         for (int v = 0; v < kAttrVariants; ++v)
             max_ctas = std::max<int64_t>(max_ctas, (int64_t)ctx->sms * ctx->occ_attr[acc][e][v]);
         for (int v = 0; v < kRepVariants; ++v)
-            max_ctas = std::max<int64_t>(max_ctas, (int64_t)ctx->sms * ctx->occ_rep[acc][e][v]);
+            max_ctas = std::max<int64_t>(max_ctas, (int64_t)ctx->sms * ctx->occ_rep[rep_acc(acc)][e][v]);
     }
     const int64_t part_units = std::max<int64_t>(P.tiles * ((max_ctas + P.tiles - 1) / P.tiles + 1),
                                                  max_ctas + 2 * P.tiles);
@@ -438,10 +508,10 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
         int best = kRepDefault;
         double best_rate = 0.0;
         for (int v = 0; v < kRepVariants; ++v) {
-            const int occ = ctx->occ_rep[acc][0][v];
+            const int occ = ctx->occ_rep[rep_acc(acc)][0][v];
             if (occ < 1) continue;
             ra.sp = make_split(tt, nblocks, (int64_t)ctx->sms * occ);
-            const double ms = timed([&] { return launch_repulsion(ra, acc, false, v, st); });
+            const double ms = timed([&] { return launch_repulsion(ra, rep_acc(acc), false, v, st); });
             const double pairs = (double)std::min<int64_t>(tt * kTile, P.N) * (double)P.N;
             const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
             snprintf(line, sizeof line, "repulsion threads=%d unroll=%d: %.4g pairs/s\n",
@@ -449,7 +519,7 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
             ctx->tune_log += line;
             if (rate > best_rate) { best_rate = rate; best = v; }
         }
-        ctx->rep_choice[acc] = best;
+        ctx->rep_choice[rep_acc(acc)] = best;
     }
     if (do_sym) {
         // a sub-triangle of about 1e11 directed pairs (the first tt tiles)
@@ -465,9 +535,10 @@ int tune_pairs(sparkling_ctx *ctx, PairPlan &P, int acc, AttrArgs aa, RepArgs ra
             const double ms = timed([&] { return launch_repulsion_sym(sa, false, v, st); });
             const double pairs = (double)sa.N * (double)(sa.N - 1);
             const double rate = ms > 0 ? pairs / (ms * 1e-3) : 0.0;
-            snprintf(line, sizeof line, "repulsion symmetric sources/lane=%d %s-paired: %.4g pairs/s\n",
-                     sym_variant_sources(v), sym_variant_source_paired(v) ? "source" : "target",
-                     rate);
+            snprintf(line, sizeof line,
+                     "repulsion symmetric threads=%d sources/lane=%d %s-paired: %.4g pairs/s\n",
+                     sym_variant_threads(v), sym_variant_sources(v),
+                     sym_variant_source_paired(v) ? "source" : "target", rate);
             ctx->tune_log += line;
             if (rate > best_rate) { best_rate = rate; best = v; }
         }
@@ -499,6 +570,9 @@ int build_field(sparkling_ctx *ctx, const sparkling_grid *g, cudaStream_t st)
     const size_t bytes = field_bytes(g->n[0], g->n[1], g->n[2]);
     ctx->field_valid = false;
     if (bytes > ctx->field_cap) {
+        int s;
+        if ((s = check_limit(ctx, held_bytes(ctx) - ctx->field_cap, bytes, "attraction field")))
+            return s;
         CK(cudaStreamSynchronize(st));
         cudaFree(ctx->field);
         ctx->field = nullptr;
@@ -598,7 +672,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
     ra.eps2 = aa.eps2;
     const bool mesh_mode = ctx->rep_mode == SPARKLING_REPULSION_MESH;
     const bool need_a = !field_mode && attr_choice_of(ctx, acc, P.gxp) < 0,
-               need_r = !mesh_mode && !ctx->rep_symmetric && ctx->rep_choice[acc] < 0,
+               need_r = !mesh_mode && !ctx->rep_symmetric && ctx->rep_choice[rep_acc(acc)] < 0,
                need_s = !mesh_mode && ctx->rep_symmetric && ctx->sym_choice < 0;
     if (ctx->autotune && (need_a || need_r || need_s)) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -607,7 +681,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
             int s = tune_pairs(ctx, P, acc, aa, ra, need_a, need_r, need_s,
                                at<unsigned long long>(ctx, P.o_racc), st);
             if (s) return s;
-            const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[acc];
+            const int va = attr_choice_of(ctx, acc, P.gxp), vr = ctx->rep_choice[rep_acc(acc)];
             set_splits(ctx, P, acc, energy, va < 0 ? kAttrDefault : va, vr < 0 ? kRepDefault : vr);
         }
     }
@@ -659,7 +733,7 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         ls.done();
     } else {
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
-        CK(launch_repulsion(ra, acc, energy, P.vr, st));
+        CK(launch_repulsion(ra, rep_acc(acc), energy, P.vr, st));
         ls.done();
     }
     CombineArgs cb{};
@@ -711,8 +785,8 @@ int common_checks(sparkling_ctx *ctx, const void *K, int K_dtype, int64_t N, con
     if (N < 2) return fail(ctx, SPARKLING_E_INVAL, "N = %lld must be >= 2", (long long)N);
     if (N > ((int64_t)1 << 31) - kTile)
         return fail(ctx, SPARKLING_E_INVAL, "N = %lld is too large", (long long)N);
-    if (acc != SPARKLING_ACC_KAHAN32 && acc != SPARKLING_ACC_FP64)
-        return fail(ctx, SPARKLING_E_INVAL, "acc %d is not KAHAN32/FP64", acc);
+    if (acc != SPARKLING_ACC_KAHAN32 && acc != SPARKLING_ACC_FP64 && acc != SPARKLING_ACC_FP64_PAIR)
+        return fail(ctx, SPARKLING_E_INVAL, "acc %d is not KAHAN32/FP64/FP64_PAIR", acc);
     if ((s = validate_grid(ctx, g, true))) return s;
     return SPARKLING_OK;
 }
@@ -759,6 +833,7 @@ int run_project(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns
     p.viol = want_viol ? reinterpret_cast<unsigned long long *>(ctx->d_small + 2) : nullptr;
     p.notconv = pr->tol > 0 ? reinterpret_cast<int *>(ctx->d_small + 6) : nullptr;
     p.gstate = L.global_state ? at<double>(ctx, L.o_state) : nullptr;
+    p.mixed = ctx->proj_mode == SPARKLING_PROJECTION_MIXED ? 1 : 0;
     if (want_viol || p.notconv)
         CK(cudaMemsetAsync(ctx->d_small + 2, 0, 5 * sizeof(double), st));
     LaunchScope ls(ctx, SPARKLING_KERNEL_PROJECT, st);
@@ -939,6 +1014,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.items = at<EngineItem>(ctx, b.o_items);
     e.n_items = (int32_t)n_items;
     e.proj_in_smem = b.proj_in_smem ? 1 : 0;
+    e.proj_mixed = ctx->proj_mode == SPARKLING_PROJECTION_MIXED ? 1 : 0;
     e.pos = at<float4>(ctx, b.o_pos);
     e.K = K;
     e.part = at<dacc4>(ctx, b.o_part);
@@ -1178,11 +1254,14 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
     ProjPlan L;
     if ((s = plan_project(ctx, K_dtype, Nc, Ns, cv, L))) return s;
     if ((s = ensure_ws(ctx, cv.off))) return s;
+    // the whole device work of the step, timed as one scope when timing is on
+    StepScope whole(ctx, st);
     if ((s = run_pairs(ctx, K, K_dtype, grid, acc, false, P, nullptr, K_dtype, nullptr, nullptr, true,
                        st)))
         return s;
     if ((s = run_project(ctx, K, K_dtype, Nc, Ns, proj, at<double>(ctx, P.o_g64), eta, L, false, st)))
         return s;
+    whole.done();
     if (proj->tol > 0) return finish_project(ctx, proj, nullptr, st);
     return SPARKLING_OK;
 }
@@ -1492,7 +1571,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     const bool use_graph = (flags & SPARKLING_BATCH_GRAPH) && cap == cudaStreamCaptureStatusNone;
     LaunchScope ls(ctx, SPARKLING_KERNEL_ENGINE, st);
     if (use_graph && b.exec && b.graph_key == key && b.graph_variant == variant &&
-        b.graph_eps2 == eps2_of(ctx)) {
+        b.graph_eps2 == eps2_of(ctx) && b.graph_proj == ctx->proj_mode) {
         CK(cudaGraphLaunch(b.exec, st));
     } else if (use_graph && b.eager_calls > 0) {
         // Capture (which records without executing) on a private stream --
@@ -1513,6 +1592,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         b.graph_key = key;
         b.graph_variant = variant;
         b.graph_eps2 = eps2_of(ctx);
+        b.graph_proj = ctx->proj_mode;
         CK(cudaGraphLaunch(b.exec, st));
     } else {
         if ((s = batch_device_work(ctx, K, K_dtype, grids, acc, variant, st))) return s;
@@ -1537,6 +1617,7 @@ SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dt
     const size_t kb = (size_t)Nc * Ns * 3 * (K_dtype == SPARKLING_F32 ? 4 : 8);
     const size_t rb = (size_t)grid->n[0] * grid->n[1] * grid->n[2] * sizeof(float);
     if (kb > ctx->h_K_bytes) {
+        if ((s = check_limit(ctx, held_bytes(ctx) - ctx->h_K_bytes, kb, "device copy of K"))) return s;
         CK(cudaDeviceSynchronize());
         cudaFree(ctx->h_K);
         ctx->h_K = nullptr;
@@ -1548,6 +1629,8 @@ SPARKLING_API int sparkling_step_host(sparkling_ctx *ctx, void *K_host, int K_dt
         ctx->h_K_bytes = kb;
     }
     if (rb > ctx->h_rho_bytes) {
+        if ((s = check_limit(ctx, held_bytes(ctx) - ctx->h_rho_bytes, rb, "device copy of rho")))
+            return s;
         CK(cudaDeviceSynchronize());
         cudaFree(ctx->h_rho);
         ctx->h_rho = nullptr;
@@ -1646,6 +1729,42 @@ SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int varian
     return fail(ctx, SPARKLING_E_INVAL, "kernel %d has no selectable shape", kernel);
 }
 
+SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (mode != SPARKLING_PROJECTION_FP64 && mode != SPARKLING_PROJECTION_MIXED)
+        return fail(ctx, SPARKLING_E_INVAL, "projection mode %d is not FP64/MIXED", mode);
+    ctx->proj_mode = mode;
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_wait_budget(sparkling_ctx *ctx, int64_t cycles)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (cycles < 0) cycles = kWaitCycles;
+    if (cycles > ((int64_t)1 << 40))
+        return fail(ctx, SPARKLING_E_INVAL, "wait budget %lld cycles is too large", (long long)cycles);
+    ctx->wait_cycles = cycles;
+    if (ctx->inited) {
+        // kernels read the budget from the control block: wait until none
+        // is running, then replace it
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaDeviceSynchronize());
+        const long long v = cycles;
+        CK(cudaMemcpy(reinterpret_cast<char *>(ctx->d_status) + offsetof(DevCtl, wait_cycles), &v,
+                      sizeof v, cudaMemcpyHostToDevice));
+    }
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_memory_limit(sparkling_ctx *ctx, int64_t bytes)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (bytes < 0) return fail(ctx, SPARKLING_E_INVAL, "memory limit must be >= 0");
+    ctx->mem_limit = (size_t)bytes;
+    return SPARKLING_OK;
+}
+
 SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode)
 {
     if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
@@ -1719,8 +1838,8 @@ SPARKLING_API int sparkling_tuning_report(const sparkling_ctx *ctx, char *buf, i
         }
     if (ctx->sym_choice >= 0) {
         char line[128];
-        snprintf(line, sizeof line, "chosen repulsion symmetric: sources/lane=%d %s-paired\n",
-                 sym_variant_sources(ctx->sym_choice),
+        snprintf(line, sizeof line, "chosen repulsion symmetric: threads=%d sources/lane=%d %s-paired\n",
+                 sym_variant_threads(ctx->sym_choice), sym_variant_sources(ctx->sym_choice),
                  sym_variant_source_paired(ctx->sym_choice) ? "source" : "target");
         r += line;
     }

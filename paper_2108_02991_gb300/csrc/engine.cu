@@ -55,15 +55,16 @@ __device__ __forceinline__ void mark_done(unsigned int *done)
 }
 
 // Bounded wait until *done >= target; false (and the timeout status bit) if
-// it does not happen within kWaitCycles.
+// it does not happen within the context's wait budget.
 __device__ bool wait_done(const unsigned int *done, unsigned int target, int *status, int *flag)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire(done) < target) {
+            const long long budget = wait_budget(status);
             const long long t0 = clock64();
             while (ld_acquire(done) < target) {
-                if (clock64() - t0 > kWaitCycles) {
+                if (clock64() - t0 > budget) {
                     atomicOr(status, kDevTimeout);
                     ok = 0;
                     break;
@@ -159,7 +160,7 @@ __device__ __noinline__ bool project_item(const EngineArgs &e, const EngineItem 
         for (int c = 0; c < 3; ++c)
             kv[c] = (double)K[3 * m + c] - eta * (g[c] - r[c] * invN);
     };
-    if (sizeof(KT) == 4)
+    if (sizeof(KT) == 4 && e.proj_mixed)
         project_shot_mixed<KT>(carve_f(reinterpret_cast<float *>(base), Ns), K, sp, loadk);
     else
         project_shot<KT>(A, K, sp, loadk);

@@ -21,6 +21,18 @@ constexpr int kDevNonFinite = 1;
 constexpr int kDevTimeout = 2;
 constexpr int kDevRange = 4;            // a sample outside the fast-repulsion mesh
 
+// Default budget of a bounded device wait, in SM clock cycles (~2 s at 2 GHz).
+constexpr long long kWaitCycles = 4000000000LL;
+
+// Device control block of a context: the status word the kernels OR their
+// error bits into and, behind it, the budget of their bounded waits.  Every
+// `int *status` a kernel receives points at the first member of one of these.
+struct DevCtl {
+    int status;
+    int reserved;
+    long long wait_cycles;   // budget of a bounded wait (cycles); the drains after a timeout use kWaitCycles
+};
+
 // Four FP64 partial sums of one target: force (x, y, z) and energy (w).
 struct __align__(32) dacc4 {
     double x, y, z, w;
@@ -178,10 +190,14 @@ int repulsion_ctas_per_sm(int acc, bool energy, int variant);
 cudaError_t launch_repulsion(const RepArgs &a, int acc, bool energy, int variant, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStream_t st);
 // Symmetric repulsion (repulsion_sym.cu): every unordered pair once.
-constexpr int kSymVariants = 3;       // sources per lane 2 / 4 (target-paired), 2 (source-paired)
+// Shapes: 256 threads (4 targets per lane) with 2 or 4 sources per lane and
+// the targets paired (0, 1) or 2 sources paired (2); 128 threads (8 targets
+// per lane), 2 sources paired (3).
+constexpr int kSymVariants = 4;
 constexpr int kSymDefault = 2;        // shape used where nothing was tuned or pinned
 int sym_variant_sources(int v);
 bool sym_variant_source_paired(int v);
+int sym_variant_threads(int v);
 size_t repulsion_sym_smem_bytes();
 int repulsion_sym_ctas_per_sm(bool energy, int variant);
 cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cudaStream_t st);
@@ -230,6 +246,7 @@ struct ProjArgs {
     double pin[3];
     int pin_index, n_iter, check_every;
     double *gstate;        // per-CTA state in global memory (18 * Ns doubles) or null
+    int mixed;             // FP32 K, fixed iterations: iterate in FP32 on the displacement
     int *status;
     unsigned long long *viol;  // optional [4] (non-negative doubles as bits)
     int *notconv;          // optional count of shots that did not certify
@@ -275,6 +292,7 @@ struct EngineArgs {
     const EngineItem *items;
     int32_t n_items;
     int32_t proj_in_smem;    // projection state fits in the shared-memory union
+    int32_t proj_mixed;      // FP32 K: the mixed-precision projection (else FP64 throughout)
     const float4 *pos;       // packed samples of all trajectories
     void *K;                 // [sum N][3], updated in place by the projection items
     dacc4 *part;

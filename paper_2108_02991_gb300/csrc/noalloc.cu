@@ -19,10 +19,10 @@
 // stream.
 //
 // All calls on a device share the one array and it keeps the previous call's
-// contents.  The status word is cleared at the start of every call; every
-// other byte a call reads it has written first.  Calls whose kernels overlap
-// on the GPU (different streams, or different host threads) race on the
-// array: serialise them.
+// contents.  The control block (status word and wait budget) is reset at the
+// start of every call; every other byte a call reads it has written first.
+// Calls whose kernels overlap on the GPU (different streams, or different
+// host threads) race on the array: serialise them.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -80,15 +80,20 @@ int scratch_for_current_device(void **out, int *sms)
     return SPARKLING_OK;
 }
 
-bool on_device(const void *p)
+// Device memory of device `dev` (the current one), or managed memory.
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
+
+// The control block every call starts from: status clear, default wait
+// budget.  Static storage, so the asynchronous copy always reads it.
+const DevCtl kFreshCtl = {0, 0, kWaitCycles};
 
 } // namespace
 
@@ -153,9 +158,13 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     int s;
     void *base = nullptr;
     int sms = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((s = scratch_for_current_device(&base, &sms))) return s;
-    if (!on_device(K) || !on_device(G) || !on_device(grid->rho))
-        return noalloc_fail(SPARKLING_E_INVAL, "K, G and grid->rho must be device memory");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(SPARKLING_E_CUDA, "cudaGetDevice failed");
+    if (!on_device(K, dev) || !on_device(G, dev) || !on_device(grid->rho, dev))
+        return noalloc_fail(SPARKLING_E_INVAL,
+                            "K, G and grid->rho must be device memory of the current device (%d)", dev);
     const int occ_a = attraction_ctas_per_sm(acc, false, kAttrDefault);
     const int occ_r = repulsion_ctas_per_sm(acc, false, kRepDefault);
     if (occ_a < 1 || occ_r < 1) {
@@ -185,14 +194,13 @@ extern "C" SPARKLING_API int sparkling_grad_noalloc(const void *K, int K_dtype, 
     p += up256((size_t)tiles * spa.slots * kTile * sizeof(dacc4));
     dacc4 *part_r = reinterpret_cast<dacc4 *>(p);
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
 #define NA_CK(call)                                                                               \
     do {                                                                                          \
         if ((e = (call)) != cudaSuccess)                                                          \
             return noalloc_fail(SPARKLING_E_CUDA, "%s: %s", #call, cudaGetErrorString(e));        \
     } while (0)
-    NA_CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+    NA_CK(cudaMemcpyAsync(status, &kFreshCtl, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
     NA_CK(launch_pack_positions(K, K_dtype, N, pos, status, sms, st));
     NA_CK(launch_pack_grid(grid->rho, nx, ny, nz, gxp, grid->lo, grid->hi, rho, coords, status, sms,
                            st));

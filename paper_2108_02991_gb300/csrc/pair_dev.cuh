@@ -20,7 +20,7 @@ __device__ void drain_stages(uint64_t *bars, uint32_t first, uint32_t count, int
 {
     if (threadIdx.x == 0)
         for (uint32_t g = first; g < first + count; ++g)
-            mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1, status);
+            mbar_wait_drain(&bars[g % kStages], (g / kStages) & 1, status);
     __syncthreads();
 }
 
@@ -60,19 +60,44 @@ template <int NT> struct SmemAcc<1, NT> {
     __device__ double value(int v) const { return p[v * NT]; }
 };
 
+// ACC 2: the plain FP64-accumulate form.  The pair terms are added to FP64
+// row sums one by one (no FP32 partial sums), and the row sums go to FP64
+// accumulators.
+template <int NT> struct SmemAcc<2, NT> {
+    double *p;
+    __device__ SmemAcc(void *base, int tid) : p(static_cast<double *>(base) + tid) {}
+    __device__ void zero(int nv)
+    {
+        for (int v = 0; v < nv; ++v) p[v * NT] = 0.0;
+    }
+    __device__ __forceinline__ void add(int v, double x) { p[v * NT] += x; }
+    __device__ double value(int v) const { return p[v * NT]; }
+};
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// Type of the row sums: FP32 for the compensated and FP64 folds, FP64 for
+// the plain FP64-accumulate form.
+template <int ACC> struct RowSum { typedef float type; };
+template <> struct RowSum<2> { typedef double type; };
+
 constexpr int kAccBytes = kTile * 3 * 8;   // 24 KB per CTA: 3 values x 8 bytes per target
 
 // NR grid rows (1 or 2) against the thread's T targets.  The rows share the
 // x coordinates, so one dx = kx - x_q feeds NR pairs.  x_q is rebuilt as
 // lo + (q + 1/2) h: kxp = kx - lo - h/2 (rounded once from double) and
 // dx = kxp - q h with one FFMA per group of 4 points.  Row sums are FP32 and
-// are added into the stage accumulators st[t][0..NV).
-template <bool ENERGY, int NR, int T>
+// are added into the stage accumulators st[t][0..NV).  AT is the type the
+// pair terms are summed in: float (row sums in FP32), or double (every pair
+// term converted and added in FP64: the plain FP64-accumulate form).
+template <bool ENERGY, int NR, int T, typename AT>
 __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const float *kxp,
                                           const float *ky, const float *kz, const float *yr,
-                                          const float *zr, float h, float eps2, float (*st)[3])
+                                          const float *zr, float h, float eps2, AT (*st)[3])
 {
-    float s2[NR][T], sw[NR][T], sx[T];
+    float s2[NR][T];
+    AT sw[NR][T], sx[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
 #pragma unroll
@@ -107,10 +132,10 @@ __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const floa
                     const float r2 = fmaf(dx[j], dx[j], s2[r][t]);
                     const float wt = rho * rsqrt_sfu(r2);
                     if (ENERGY) {
-                        sw[r][t] = fmaf(wt, r2, sw[r][t]);     // rho * |d|
+                        sw[r][t] = fma_t((AT)wt, (AT)r2, sw[r][t]);     // rho * |d|
                     } else {
-                        sw[r][t] += wt;
-                        sx[t] = fmaf(wt, dx[j], sx[t]);
+                        sw[r][t] += (AT)wt;
+                        sx[t] = fma_t((AT)wt, (AT)dx[j], sx[t]);
                     }
                 }
             }
@@ -126,8 +151,8 @@ __device__ __forceinline__ void attr_rows(const float *rows, int gxp, const floa
             st[t][0] += sx[t];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                st[t][1] = fmaf(ky[t] - yr[r], sw[r][t], st[t][1]);
-                st[t][2] = fmaf(kz[t] - zr[r], sw[r][t], st[t][2]);
+                st[t][1] = fma_t((AT)(ky[t] - yr[r]), sw[r][t], st[t][1]);
+                st[t][2] = fma_t((AT)(kz[t] - zr[r]), sw[r][t], st[t][2]);
             }
         }
     }
@@ -182,9 +207,10 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
         const int64_t rs = r0 + (int64_t)s * R;
         const int nrows = (int)((rs + R < r1 ? rs + R : r1) - rs);
         int iy = (int)(rs % a.ny), iz = (int)(rs / a.ny);
-        float st[T][3];
+        typedef typename RowSum<ACC>::type AT;
+        AT st[T][3];
 #pragma unroll
-        for (int t = 0; t < T; ++t) st[t][0] = st[t][1] = st[t][2] = 0.f;
+        for (int t = 0; t < T; ++t) st[t][0] = st[t][1] = st[t][2] = (AT)0;
         int rr = 0;
         for (; rr + 1 < nrows; rr += 2) {
             float yr[2], zr[2];
@@ -192,11 +218,11 @@ __device__ bool attraction_segment(const AttrArgs &a, int64_t tile, int64_t r0, 
             if (++iy == a.ny) { iy = 0; ++iz; }
             yr[1] = ys[iy]; zr[1] = zs[iz];
             if (++iy == a.ny) { iy = 0; ++iz; }
-            attr_rows<ENERGY, 2, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
+            attr_rows<ENERGY, 2, T, AT>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
         }
         if (rr < nrows) {
             float yr[1] = {ys[iy]}, zr[1] = {zs[iz]};
-            attr_rows<ENERGY, 1, T>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
+            attr_rows<ENERGY, 1, T, AT>(buf + rr * gxp, gxp, kxp, ky, kz, yr, zr, a.hx, a.eps2, st);
         }
 #pragma unroll
         for (int t = 0; t < T; ++t)

@@ -20,7 +20,8 @@
 // - eps = 1e-30 added to r^2 makes a zero difference contribute exactly 0
 //   without a branch (the minimum-norm subgradient of |.| at 0);
 // - row / block sums are FP32 and folded per target into a compensated FP32
-//   (TwoSum) or an FP64 accumulator;
+//   (TwoSum) or an FP64 accumulator; the plain FP64-accumulate form of the
+//   attraction (acc 2) adds every pair term in FP64 instead, for comparison;
 // - the flattened (tile, unit) space is split evenly over one wave of
 //   persistent CTAs; each CTA writes one FP64 partial per tile it touches and
 //   a combine kernel adds the partials in a fixed order (deterministic).
@@ -222,6 +223,7 @@ template <int NT>
 void *pick_attraction_nt(int acc, bool energy)
 {
     if (acc == 0) return energy ? attraction_fn<0, true, NT>() : attraction_fn<0, false, NT>();
+    if (acc == 2) return energy ? attraction_fn<2, true, NT>() : attraction_fn<2, false, NT>();
     return energy ? attraction_fn<1, true, NT>() : attraction_fn<1, false, NT>();
 }
 

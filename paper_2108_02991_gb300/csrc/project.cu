@@ -10,6 +10,10 @@
 // The output is s(q).  With a gradient G the shot is first stepped:
 // k = K - eta G (eq. proj_grad_descent).
 //
+// FP32 samples may instead (an opt-in of the context) iterate in FP32 on the
+// displacement s - k and the duals (project_shot_mixed); FP64 is the default
+// for every sample type.
+//
 // One CTA per shot (grid-stride over shots).  The 18 per-sample FP64 arrays
 // (k, s, y1, y2, q1, q2; x, y, z each, structure of arrays so that a warp
 // touches consecutive doubles) live in shared memory when they fit and in a
@@ -54,8 +58,8 @@ __global__ void __launch_bounds__(kProjMaxThreads) project_kernel(const ProjArgs
                 if (G) kv[c] -= eta * G[3 * (off + m) + c];
             }
         };
-        if (sizeof(KT) == 4 && p.tol <= 0.0) {
-            // FP32 output, fixed iterations: the mixed-precision form
+        if (sizeof(KT) == 4 && p.tol <= 0.0 && p.mixed) {
+            // FP32 output, fixed iterations, asked for: the mixed-precision form
             project_shot_mixed<KT>(carve_f(reinterpret_cast<float *>(base), Ns), K + 3 * off, sp,
                                    loadk);
             if (p.viol) record_violation<KT>(K + 3 * off, sp);

@@ -7,9 +7,6 @@
 
 namespace sparkling {
 
-// A bounded wait gives up after this many SM clock cycles (~2 s at 2 GHz).
-constexpr long long kWaitCycles = 4000000000LL;
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -45,20 +42,43 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for phase `parity` of the barrier to complete, for at most
-// kWaitCycles.  On timeout sets kDevTimeout in *status and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status)
+// The wait budget (SM clock cycles) of the context whose status word this is.
+__device__ __forceinline__ long long wait_budget(const int *status)
+{
+    return reinterpret_cast<const volatile DevCtl *>(status)->wait_cycles;
+}
+
+// Wait for phase `parity` of the barrier to complete, for at most `budget`
+// cycles.  On timeout sets kDevTimeout in *status and returns false.
+__device__ __forceinline__ bool mbar_wait_cycles(uint64_t *bar, uint32_t parity, int *status,
+                                                 long long budget)
 {
     if (mbar_try_wait(bar, parity))
         return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             atomicOr(status, kDevTimeout);
             return false;
         }
     }
     return true;
+}
+
+// A wait on data a copy delivers, with the context's budget.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    return mbar_wait_cycles(bar, parity, status, wait_budget(status));
+}
+
+// After a timeout: wait (with the fixed default budget, whatever the
+// context's) for a copy still in flight, so that no bulk copy writes into
+// shared memory once the CTA has exited.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity, int *status)
+{
+    return mbar_wait_cycles(bar, parity, status, kWaitCycles);
 }
 
 // Arm the barrier for `bytes` of transaction and start a bulk copy of `bytes`

@@ -6,10 +6,10 @@
 //
 // Work: the upper triangle of tile pairs (I, J), I <= J, tiles of 1024
 // samples, split evenly over one wave of persistent CTAs (contiguous runs of
-// a row share the target tile I).  In a CTA, warp w holds 128 targets of
-// tile I (4 per lane) and, in round r, the 32*S sources of chunk
-// (w + r) mod (1024 / 32S) of tile J (S per lane, the tile staged by a TMA
-// bulk copy).  The sources and their accumulators rotate one lane per step
+// a row share the target tile I).  A CTA of NT threads (256 or 128) holds the
+// 1024 targets of tile I, T = 1024/NT per lane (4 or 8): warp w holds 32*T
+// of them and, in round r, the 32*S sources of chunk (w + r) mod
+// (1024 / 32S) of tile J (S per lane, the tile staged by a TMA bulk copy).  The sources and their accumulators rotate one lane per step
 // through the 32 lanes, so after 32 steps every (target, source) pair of the
 // two chunks has met once and each source is back home; its accumulator is
 // then added to a shared-memory j-accumulator, which no other warp touches
@@ -32,20 +32,21 @@ namespace sparkling {
 
 namespace {
 
-constexpr int kSymThreads = 256;
-constexpr int kSymWarps = kSymThreads / 32;
-constexpr int kSymT = 4;                       // targets per lane
 constexpr int kSymStages = 2;                  // J tiles in flight
-static_assert(kSymWarps * 32 * kSymT == kTile, "a CTA holds one tile of targets");
+// NT threads per CTA hold one tile of targets, T = kTile / NT per lane.
 // S sources per lane: a chunk is 32*S sources, a tile kTile/(32*S) chunks;
 // in round r warp w owns chunk (w + r) mod chunks.
 
 // Shared memory: mbarriers | J-tile stages | FP32 j-accumulator [NV][1024] |
-// per-thread int64 i-accumulators [T*NV][256].
+// per-thread int64 i-accumulators [T*NV][NT] (T * NT = kTile).
 constexpr size_t kSymHead = 64;
 constexpr size_t kSymStageBytes = (size_t)kTile * sizeof(float4);
 constexpr size_t kSymJaccBytes = 3 * kTile * sizeof(float);
-constexpr size_t kSymIaccBytes = (size_t)kSymT * 3 * kSymThreads * sizeof(long long);
+constexpr size_t kSymIaccBytes = (size_t)kTile * 3 * sizeof(long long);
+
+// Resident CTAs asked of the compiler: 2 of 256 threads (<= 128 registers),
+// 3 of 128 threads (<= 168 registers, 8 targets per lane).
+constexpr int sym_min_ctas(int nt) { return nt >= 256 ? 2 : 3; }
 
 __device__ __forceinline__ long long to_fix(float x)
 {
@@ -57,19 +58,19 @@ __device__ __forceinline__ void add_fix(unsigned long long *p, long long v)
     if (v != 0) atomicAdd(p, (unsigned long long)v);
 }
 
-// One off-diagonal item: the thread's kSymT targets against tile J (in src,
+// One off-diagonal item: the thread's T = kTile/NT targets against tile J (in src,
 // jvalid valid sources).  Target sums go to ai (registers), source sums to
 // jacc ([NV][kTile], shared).  RAGGED: the last tile is partial; tm/sm mask
 // the missing targets/sources to zero.
-template <bool ENERGY, bool RAGGED, int S>
+template <bool ENERGY, bool RAGGED, int S, int NT>
 __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const float *tx,
                                          const float *ty, const float *tz, const float *tm,
                                          float eps2, float (*ai)[3], float *jacc)
 {
-    constexpr int T = kSymT;
+    constexpr int T = kTile / NT;
     constexpr int P = T / 2;                    // target pairs (paired FP32 lanes)
     constexpr int kSymChunk = 32 * S, kChunks = kTile / kSymChunk;
-    static_assert(kChunks >= kSymWarps && (kChunks & (kChunks - 1)) == 0, "chunk count");
+    static_assert(kChunks >= NT / 32 && (kChunks & (kChunks - 1)) == 0, "chunk count");
     static_assert(T % 2 == 0, "targets are processed in pairs");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int from = (lane + 1) & 31;
@@ -189,14 +190,14 @@ __device__ __forceinline__ void sym_item(const float4 *src, int jvalid, const fl
 // distance steps and 3 + 3 accumulations, all paired -- 12 FP32 lane
 // operations per unordered pair -- and the source sums stay paired while
 // they rotate.  The target sums are folded once per item.
-template <bool ENERGY, bool RAGGED>
+template <bool ENERGY, bool RAGGED, int NT>
 __device__ __forceinline__ void sym_item_sp(const float4 *src, int jvalid, const float *tx,
                                             const float *ty, const float *tz, const float *tm,
                                             float eps2, float (*ai)[3], float *jacc)
 {
-    constexpr int T = kSymT;
+    constexpr int T = kTile / NT;
     constexpr int kChunk = 64, kChunks = kTile / kChunk;
-    static_assert(kChunks >= kSymWarps && (kChunks & (kChunks - 1)) == 0, "chunk count");
+    static_assert(kChunks >= NT / 32 && (kChunks & (kChunks - 1)) == 0, "chunk count");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int from = (lane + 1) & 31;
     f2 TX[T], TY[T], TZ[T], TM[T], AX[T], AY[T], AZ[T];
@@ -287,12 +288,12 @@ __device__ __forceinline__ void sym_item_sp(const float4 *src, int jvalid, const
 // tile, directed (each ordered pair once, target side only; the self term
 // contributes nothing to the force and eps to the energy, which the energy
 // reduction removes).
-template <bool ENERGY>
+template <bool ENERGY, int NT>
 __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const float *tx,
                                           const float *ty, const float *tz, float eps2,
                                           float (*ai)[3])
 {
-    constexpr int T = kSymT;
+    constexpr int T = kTile / NT;
 #pragma unroll 2
     for (int j = 0; j < jvalid; ++j) {
         const float4 q = src[j];
@@ -312,18 +313,18 @@ __device__ __forceinline__ void diag_item(const float4 *src, int jvalid, const f
     }
 }
 
-constexpr int kSymTargetsPerWarp = 32 * kSymT;   // 128
-
 // REG: the regularisation eps^2 is a kernel argument; without it the
 // zero-distance guard kEps2 is a compile-time constant of the pair loop.
 // BATCHED: the units of a.B trajectories (a.traj), else of one.
 // SP: the source-paired item (two sources per lane), else the target-paired
-// item with S sources per lane.
-template <bool ENERGY, int S, bool SP, bool REG, bool BATCHED>
-__global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const SymArgs a)
+// item with S sources per lane.  NT: threads per CTA (T = 1024/NT targets per
+// lane).
+template <bool ENERGY, int S, bool SP, bool REG, bool BATCHED, int NT>
+__global__ void __launch_bounds__(NT, sym_min_ctas(NT)) repulsion_sym_kernel(const SymArgs a)
 {
     const float eps2 = REG ? a.eps2 : kEps2;
-    constexpr int T = kSymT;
+    constexpr int T = kTile / NT;
+    constexpr int kTargetsPerWarp = 32 * T;
     constexpr int NV = ENERGY ? 1 : 3;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -383,16 +384,15 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
     }
     int curB = -1;
     int64_t curI = -1;
-    float tx[T], ty[T], tz[T], tm[T];
-    // the thread's targets of tile curI: l = warp*128 + t*32 + lane
+    // the thread's targets of tile curI: l = warp*32T + t*32 + lane
     auto flush_i = [&]() {
         const int64_t nb = tr_n(curB), ob = tr_off(curB);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const int64_t i = curI * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
+            const int64_t i = curI * kTile + warp * kTargetsPerWarp + t * 32 + lane;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                long long &x = iacc[(t * NV + v) * kSymThreads + tid];
+                long long &x = iacc[(t * NV + v) * NT + tid];
                 if (i < nb) add_fix(&a.acc[(ob + i) * NV + v], x);
                 x = 0;
             }
@@ -403,22 +403,29 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
             if (curI >= 0) flush_i();
             curI = I;
             curB = b;
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * NT + tid] = 0;
+        }
+        // The targets are read again for every item (from L2): nothing but
+        // the loop state stays in registers between items.
+        float tx[T], ty[T], tz[T], tm[T];
+        {
             const int64_t nb = tr_n(b), ob = tr_off(b);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                const int64_t i = I * kTile + warp * kSymTargetsPerWarp + t * 32 + lane;
+                const int64_t i = I * kTile + warp * kTargetsPerWarp + t * 32 + lane;
                 const bool ok = i < nb;
                 const float4 p = ok ? a.pos[ob + i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 tx[t] = p.x; ty[t] = p.y; tz[t] = p.z; tm[t] = ok ? 1.f : 0.f;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * kSymThreads + tid] = 0;
             }
         }
         const bool ok = mbar_wait_bounded(&bars[g % kSymStages], (g / kSymStages) & 1, a.status);
         if (__syncthreads_or(!ok)) {
             if (tid == 0)
                 for (uint32_t h = g; h < n && h < g + kSymStages; ++h)
-                    mbar_wait_bounded(&bars[h % kSymStages], (h / kSymStages) & 1, a.status);
+                    mbar_wait_drain(&bars[h % kSymStages], (h / kSymStages) & 1, a.status);
             __syncthreads();
             return;
         }
@@ -428,22 +435,22 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
 #pragma unroll
         for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
         if (I == J) {
-            diag_item<ENERGY>(src, jvalid, tx, ty, tz, eps2, ai);
+            diag_item<ENERGY, NT>(src, jvalid, tx, ty, tz, eps2, ai);
         } else {
-            for (int e = tid; e < NV * kTile; e += kSymThreads) jacc[e] = 0.f;
+            for (int e = tid; e < NV * kTile; e += NT) jacc[e] = 0.f;
             __syncthreads();
             if (SP) {
                 if (jvalid < kTile)
-                    sym_item_sp<ENERGY, true>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                    sym_item_sp<ENERGY, true, NT>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
                 else
-                    sym_item_sp<ENERGY, false>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                    sym_item_sp<ENERGY, false, NT>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
             } else {
                 if (jvalid < kTile)
-                    sym_item<ENERGY, true, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                    sym_item<ENERGY, true, S, NT>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
                 else
-                    sym_item<ENERGY, false, S>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
+                    sym_item<ENERGY, false, S, NT>(src, jvalid, tx, ty, tz, tm, eps2, ai, jacc);
             }
-            for (int l = tid; l < jvalid; l += kSymThreads)
+            for (int l = tid; l < jvalid; l += NT)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
                     add_fix(&a.acc[(tr_off(b) + J * kTile + l) * NV + v], to_fix(jacc[v * kTile + l]));
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
 #pragma unroll
         for (int t = 0; t < T; ++t)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * kSymThreads + tid] += to_fix(ai[t][v]);
+            for (int v = 0; v < NV; ++v) iacc[(t * NV + v) * NT + tid] += to_fix(ai[t][v]);
         __syncthreads();   // stage g consumed, jacc flushed
         if (g + kSymStages < n) {
             if (tid == 0) {
@@ -468,9 +475,10 @@ __global__ void __launch_bounds__(kSymThreads, 2) repulsion_sym_kernel(const Sym
 template <bool E, bool REG, bool BATCHED>
 void *sym_fn_reg(int variant)
 {
-    if (variant == 1) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, false, REG, BATCHED>);
-    if (variant == 2) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, true, REG, BATCHED>);
-    return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, false, REG, BATCHED>);
+    if (variant == 1) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 4, false, REG, BATCHED, 256>);
+    if (variant == 2) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, true, REG, BATCHED, 256>);
+    if (variant == 3) return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, true, REG, BATCHED, 128>);
+    return reinterpret_cast<void *>(repulsion_sym_kernel<E, 2, false, REG, BATCHED, 256>);
 }
 
 template <bool E>
@@ -483,7 +491,8 @@ void *sym_fn(int variant, bool reg = true, bool batched = false)
 } // namespace
 
 int sym_variant_sources(int v) { return v == 1 ? 4 : 2; }
-bool sym_variant_source_paired(int v) { return v == 2; }
+bool sym_variant_source_paired(int v) { return v >= 2; }
+int sym_variant_threads(int v) { return v == 3 ? 128 : 256; }
 
 size_t repulsion_sym_smem_bytes()
 {
@@ -503,7 +512,8 @@ int repulsion_sym_ctas_per_sm(bool energy, int variant)
             cudaSuccess)
             return 0;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kSymThreads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sym_variant_threads(variant), smem) !=
+            cudaSuccess)
             return 0;
         best = n < best ? n : best;
     }
@@ -515,7 +525,7 @@ cudaError_t launch_repulsion_sym(const SymArgs &a, bool energy, int variant, cud
     const bool reg = a.eps2 > kEps2, batched = a.traj != nullptr;
     void *fn = energy ? sym_fn<true>(variant, reg, batched) : sym_fn<false>(variant, reg, batched);
     void *args[] = {const_cast<SymArgs *>(&a)};
-    return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(kSymThreads), args,
+    return cudaLaunchKernel(fn, dim3((unsigned)a.ctas), dim3(sym_variant_threads(variant)), args,
                             repulsion_sym_smem_bytes(), st);
 }
 

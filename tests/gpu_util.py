@@ -28,8 +28,15 @@ def assert_grad_close(gpu, ref, what="G", rel=GRAD_REL_L2, atol=GRAD_ABS):
     return e, m
 
 
+# FP32 output of the FP64 projection (the default for every K dtype): the
+# GPU's and the oracle's FP64 iterates agree to ~1e-11, so their FP32
+# roundings differ by at most one ulp of |s| <= 1/2, i.e. 2^-24.
+PROJ_F32_ROUND = 2.0 ** -24
+
+
 def proj_tol_f32(ref, k) -> float:
-    """Elementwise gate of a projection with FP32 output.  The FP32 output
+    """Elementwise gate of the opt-in mixed-precision projection (FP32
+    output, PROJECTION_MIXED).  The FP32 output
     rounds s (<= 2^-24 at |s| <= 1/2, doubled: 1.2e-7); the FP32 iteration
     of the mixed-precision form works on the displacement e = s - k and the
     duals, whose roundings (a few per iteration, accumulating over the

@@ -1,7 +1,13 @@
-"""Particle-mesh long-range part of the repulsion, plain NumPy (FP64).
+"""Particle-mesh long-range part of the repulsion, plain NumPy (FP64): a
+diagnostic restatement of the library's own mesh design.
 
-TEST INFRASTRUCTURE: only tests/ may import this module; it shares nothing
-with the CUDA library.
+NOT AN ORACLE.  It follows the same steps as the library's mesh summation
+(window, taper, guard cells, deconvolution), so a mistake in that design
+would be shared by both; no test's pass or fail rests on it.  The mesh
+tests gate the library against the exact direct sum (the oracle) within a
+stated method-error bound, and print this module's result beside it to help
+read a failure.  Only tests/ import it; it shares nothing with the CUDA
+library.
 
 The paper evaluates the repulsion with a fast multipole method (Sec. II-C.2)
 because the direct sum is O(N^2).  The library's fast repulsion is a

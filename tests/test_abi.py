@@ -147,10 +147,25 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert L.sparkling_set_shape(None, 1, 0) == lib.E_INVAL
     assert L.sparkling_set_shape(h, 0, 0) == lib.E_INVAL          # pack has no shapes
     assert L.sparkling_set_shape(h, 1, 3) == lib.E_INVAL
-    assert L.sparkling_set_shape(h, 2, 3) == lib.E_INVAL
+    assert L.sparkling_set_shape(h, 2, 4) == lib.E_INVAL
     assert L.sparkling_set_shape(h, 2, -2) == lib.E_INVAL
-    for k, v in ((1, 2), (1, -1), (2, 2), (2, -1)):
+    for k, v in ((1, 2), (1, -1), (2, 2), (2, 3), (2, -1)):
         assert L.sparkling_set_shape(h, k, v) == lib.OK
+    # projection arithmetic, wait budget, memory cap (host-side settings)
+    assert L.sparkling_set_projection(h, 2) == lib.E_INVAL
+    assert L.sparkling_set_projection(None, 0) == lib.E_INVAL
+    for m in (lib.PROJECTION_MIXED, lib.PROJECTION_FP64):
+        assert L.sparkling_set_projection(h, m) == lib.OK
+    assert L.sparkling_set_wait_budget(h, (1 << 40) + 1) == lib.E_INVAL
+    assert L.sparkling_set_wait_budget(h, 0) == lib.OK          # no CUDA call before first use
+    assert L.sparkling_set_wait_budget(h, -1) == lib.OK
+    assert L.sparkling_set_memory_limit(h, -5) == lib.E_INVAL
+    assert L.sparkling_set_memory_limit(h, 1 << 20) == lib.OK
+    assert L.sparkling_set_memory_limit(h, 0) == lib.OK
+    # the plain FP64-accumulate mode is an accepted accumulation mode
+    assert grad(acc=lib.ACC_FP64_PAIR, K=None) == lib.E_INVAL and "K is NULL" in \
+        lib.sparkling_last_error(ctx)
+    assert grad(acc=3) == lib.E_INVAL and "acc" in lib.sparkling_last_error(ctx)
     # attraction mode
     assert L.sparkling_set_attraction(h, 7) == lib.E_INVAL
     assert L.sparkling_set_attraction(h, lib.ATTRACTION_FIELD) == lib.OK

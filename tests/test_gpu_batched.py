@@ -5,7 +5,7 @@ import pytest
 
 import inputs
 import oracle
-from gpu_util import GRAD_ABS, assert_grad_close, proj_tol_f32
+from gpu_util import GRAD_ABS, PROJ_F32_ROUND, assert_grad_close, proj_tol_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -66,24 +66,35 @@ def oracle_step(K, g, p, eta, Ns):
                        p.n_iter)
 
 
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_batched_step_matches_oracle_every_sample(sp, ctx, dtype):
+@pytest.mark.parametrize("dtype,mixed", [(np.float64, False), (np.float32, False),
+                                         (np.float32, True)])
+def test_batched_step_matches_oracle_every_sample(sp, dtype, mixed):
     """Five trajectories (1..21 shots of 64 samples, ragged tiles), grids of
     different shapes (rows not a multiple of 4, a one-cell grid), per-
-    trajectory alpha, beta, eta and pins; one eager call."""
+    trajectory alpha, beta, eta and pins; one eager call.  FP32 samples with
+    the default FP64 projection and with the opt-in mixed form."""
     Ns = 64
     shots = [3, 1, 21, 7, 2]
     shapes = [(9, 5, 4), (1, 1, 1), (16, 16, 16), (13, 3, 7), (4, 4, 4)]
     Ks, grids, projs, etas = make_batch(1, shots, Ns, shapes, dtype)
-    off, outs = run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph=False)
+    c = sp.sparkling_create(0)
+    try:
+        if mixed:
+            sp.sparkling_set_projection(c, sp.PROJECTION_MIXED)
+        off, outs = run_batched(sp, c, Ks, grids, projs, etas, Ns, graph=False)
+    finally:
+        c.close()
     out = outs[0]
     for b in range(len(Ks)):
         ref = oracle_step(Ks[b], grids[b], projs[b], etas[b], Ns)
         got = out[off[b]:off[b + 1]].astype(np.float64)
         # the step moves by eta * G: a gradient within GRAD_ABS per component
         # moves the result by at most ~eta * GRAD_ABS (factor 4 for the
-        # finitely many FISTA iterations), plus one f32 ulp of 1/2 for f32 K
-        tol = 4 * etas[b] * GRAD_ABS + (proj_tol_f32(ref, Ks[b]) if dtype == np.float32 else 0.0)
+        # finitely many FISTA iterations), plus the FP32 output rounding (one
+        # ulp of 1/2) or the mixed form's bound
+        tol = 4 * etas[b] * GRAD_ABS
+        if dtype == np.float32:
+            tol += proj_tol_f32(ref, Ks[b]) if mixed else PROJ_F32_ROUND
         want = ref if dtype == np.float64 else ref.astype(np.float32).astype(np.float64)
         np.testing.assert_allclose(got, want, rtol=0, atol=tol)
 
@@ -123,8 +134,10 @@ def test_batched_graph_replay_is_bitwise_the_eager_step(sp, ctx):
 def test_batched_workload_sampled(sp, ctx):
     """The batched workload at full size: 64 trajectories of 512-sample shots,
     N_b = 512 * U{32..512}, 64^3 Gaussian densities, uneven alpha/beta; per
-    trajectory 2 shots checked against the oracle projection of
-    K - eta G, with G from sparkling_grad on that trajectory."""
+    trajectory 2 shots of the step's projection checked against the oracle
+    projection of K - eta G, with G from sparkling_grad on that trajectory
+    (the engine's own gradient is checked against the oracle in
+    test_batched_workload_gradient)."""
     probs = inputs.make_batched(seed=0)
     Ns = 512
     off = np.concatenate([[0], np.cumsum([p.N for p in probs])])
@@ -150,4 +163,31 @@ def test_batched_workload_sampled(sp, ctx):
             ref = oracle.project(half[sl], 1, Ns, p.proj.alpha, p.proj.beta, p.proj.box, -1,
                                  (0.0, 0.0, 0.0), p.proj.n_iter)
             np.testing.assert_allclose(out[sl], ref.astype(np.float32), rtol=0,
-                                       atol=proj_tol_f32(ref, half[sl]))
+                                       atol=PROJ_F32_ROUND + 4 * p.eta * GRAD_ABS)
+
+
+def test_batched_workload_gradient(sp, ctx):
+    """The engine's gradient on the full batched workload (64 trajectories,
+    9.07M samples) against the oracle on 64 random targets of every
+    trajectory.  alpha = beta = inf and a loose box make the projection the
+    identity, so K' = K - eta G exposes G = (K - K') / eta; K in FP64 keeps
+    that difference exact to ~1e-16 / eta."""
+    probs = inputs.make_batched(seed=0)
+    Ns = 512
+    off = np.concatenate([[0], np.cumsum([p.N for p in probs])])
+    K64 = np.concatenate([p.K for p in probs]).astype(np.float64)
+    K = torch.from_numpy(K64).cuda()
+    rhos = [torch.from_numpy(p.grid.rho).cuda() for p in probs]
+    gs = [sp.make_grid(r, p.grid.lo, p.grid.hi, p.grid.n) for r, p in zip(rhos, probs)]
+    ps = [sp.make_proj(INF, INF, 10.0, 2) for _ in probs]
+    etas = [p.eta for p in probs]
+    sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=False)
+    sp.sparkling_status(ctx)
+    out = K.cpu().numpy()
+    rng = np.random.default_rng(8)
+    for b, p in enumerate(probs):
+        idx = np.sort(rng.choice(p.N, size=64, replace=False))
+        Kb = K64[off[b]:off[b + 1]]
+        G = (Kb[idx] - out[off[b]:off[b + 1]][idx]) / etas[b]
+        _, _, G0 = oracle.forces(Kb, p.grid, targets=idx)
+        assert_grad_close(G, G0, f"engine G of trajectory {b} (N = {p.N}), 64 targets")

@@ -168,12 +168,20 @@ def test_field_error_against_direct_sum_small(sp, ctx):
     assert eG < 1e-2
 
 
+# Method-error targets of the field attraction against the exact direct sum
+# (relative L2 over the sampled targets; measured: 192^3 A 1.2e-4, G 1.1e-4;
+# 256^3 A 2.2e-5, G 1.8e-4): the trilinear interpolation's error falls with
+# the square of the cell size.
+FIELD_TARGETS = {"diff": (3e-4, 3e-4), "hr": (5e-5, 4e-4)}
+
+
 @pytest.mark.parametrize("name,m", [("diff", 256), ("hr", 128)])
-def test_field_full_size_sampled_targets(sp, ctx, name, m):
-    """Full-size workloads (192^3 and 256^3 densities): on sampled targets
+def test_field_full_size_sampled_targets(sp, ctx, name, m, request):
+    """Full-size workloads (192^3 and 256^3 densities): on m sampled targets
     the library returns the trilinear interpolation of the oracle's values
-    at the 8 surrounding nodes (parity), and the error of the method against
-    the oracle's direct sum is reported."""
+    at the 8 surrounding nodes (parity); the method's error against the
+    oracle's direct sum is held to FIELD_TARGETS on 4096 (diff) / 8192 (HR)
+    random targets."""
     p = inputs.make_problem(name)
     idx = np.sort(np.random.default_rng(15).choice(p.N, size=m, replace=False))
     A, G = field_grad(sp, ctx, p.K, p.grid)
@@ -182,11 +190,18 @@ def test_field_full_size_sampled_targets(sp, ctx, name, m):
     scale = np.abs(want[:, :3]).max()
     d = np.abs(A[idx] - want[:, :3]).max()
     assert d <= 1e-6 * scale, f"{name}: field differs from the node interpolation by {d:.3e}"
-    A0, _, G0 = oracle.forces(K, p.grid, targets=idx)
-    eA = rel_l2(A[idx], A0)
-    eG = rel_l2(G[idx], G0)
-    print(f"field attraction {name} {p.grid.n[0]}^3: A rel L2 {eA:.3e}, G rel L2 {eG:.3e}")
-    assert eA < 3e-3
+    if name == "hr":
+        _, big, A0, _, G0 = request.getfixturevalue("hr_oracle")
+    else:
+        big = np.sort(np.random.default_rng(16).choice(p.N, size=4096, replace=False))
+        A0, _, G0 = oracle.forces(K, p.grid, targets=big)
+    eA = rel_l2(A[big], A0)
+    eG = rel_l2(G[big], G0)
+    print(f"field attraction {name} {p.grid.n[0]}^3: A rel L2 {eA:.3e}, G rel L2 {eG:.3e} "
+          f"on {big.size} targets")
+    tA, tG = FIELD_TARGETS[name]
+    assert eA < tA
+    assert eG < tG
 
 
 def test_field_rebuilt_after_density_change(sp, ctx):

@@ -11,7 +11,7 @@ import pytest
 
 import inputs
 import oracle
-from gpu_util import assert_grad_close, proj_tol_f32, rel_l2
+from gpu_util import PROJ_F32_ROUND, assert_grad_close, proj_tol_f32, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -210,10 +210,42 @@ def test_project_shapes(sp, ctx, Nc, Ns, dt, kw):
     out = Kd.cpu().numpy().astype(np.float64)
     if dt == np.float64:
         np.testing.assert_allclose(out, ref, rtol=0, atol=1e-11)
-    else:
-        np.testing.assert_allclose(out, ref.astype(np.float32), rtol=0, atol=proj_tol_f32(ref, K))
+    else:       # FP64 iteration (the default), one rounding to FP32
+        np.testing.assert_allclose(out, ref.astype(np.float32), rtol=0, atol=PROJ_F32_ROUND)
     vref = oracle.violation(out, Nc, Ns, pr.alpha, pr.beta, pr.box, pr.pin_index, tuple(pr.pin))
     np.testing.assert_allclose(v, vref, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("Nc,Ns,kw", [
+    (9, 512, dict(pin_index=256)),
+    (3, 2560, dict(pin_index=1280)),
+    (2, 65536, dict()),
+])
+def test_project_mixed_precision_opt_in(sp, Nc, Ns, kw):
+    """PROJECTION_MIXED: FP32 samples iterate in FP32 on the displacement;
+    gated by the mixed form's bound.  FP64 samples keep the FP64 iteration
+    in that mode too."""
+    rng = np.random.default_rng(Nc * 1000 + Ns)
+    K = np.cumsum(rng.normal(scale=2e-3, size=(Nc, Ns, 3)), axis=1).reshape(-1, 3)
+    K = np.clip(K, -0.45, 0.45).astype(np.float32)
+    base = dict(alpha=1.0 / (2 * Ns), beta=1.0 / (8 * Ns * Ns), n_iter=60)
+    base.update(kw)
+    pr = sp.make_proj(**base)
+    ref = oracle_project(K, Nc, Ns, pr)
+    c = sp.sparkling_create(0)
+    try:
+        sp.sparkling_set_projection(c, sp.PROJECTION_MIXED)
+        Kd = dev(K)
+        sp.sparkling_project(c, Kd, Nc, Ns, pr)
+        sp.sparkling_status(c)
+        np.testing.assert_allclose(Kd.cpu().numpy(), ref.astype(np.float32), rtol=0,
+                                   atol=proj_tol_f32(ref, K))
+        K64 = dev(K.astype(np.float64))
+        sp.sparkling_project(c, K64, Nc, Ns, pr)
+        sp.sparkling_status(c)
+        np.testing.assert_allclose(K64.cpu().numpy(), ref, rtol=0, atol=1e-11)
+    finally:
+        c.close()
 
 
 def test_project_converged_feasible(sp, ctx):
@@ -282,3 +314,56 @@ def test_nonfinite_input_reported(sp, ctx):
     with pytest.raises(sp.SparklingError) as e:
         sp.sparkling_status(ctx)
     assert e.value.code == sp.E_NONFINITE
+
+
+def test_plain_fp64_accumulation_mode(sp, ctx):
+    """ACC_FP64_PAIR, the plain FP64-accumulate form (every attraction pair
+    term added in FP64): A, R, G and the energy against the oracle on a
+    ragged problem (3 target tiles, rows not a multiple of 4), in every
+    attraction shape."""
+    rng = np.random.default_rng(41)
+    K = rng.uniform(-0.5, 0.5, size=(2500, 3)).astype(np.float32)
+    grid = random_grid(11, 6, 9, seed=42)
+    A0, R0, G0 = oracle.forces(K.astype(np.float64), grid)
+    _, Fa0, Fr0 = oracle.energy(K.astype(np.float64), grid)
+    for v in range(3):
+        c = sp.sparkling_create(0)
+        try:
+            sp.sparkling_set_shape(c, "attraction", v)
+            G, A, R = gpu_grad(sp, c, K, grid, acc=sp.ACC_FP64_PAIR)
+            g = sp.make_grid(dev(grid.rho), grid.lo, grid.hi, grid.n)
+            F, Fa, Fr = sp.sparkling_energy(c, dev(K), g, sp.ACC_FP64_PAIR)
+        finally:
+            c.close()
+        assert_grad_close(A, A0, f"A (plain FP64 accumulation, shape {v})")
+        assert_grad_close(R, R0, f"R (plain FP64 accumulation, shape {v})")
+        assert_grad_close(G, G0, f"G (plain FP64 accumulation, shape {v})")
+        assert Fa == pytest.approx(Fa0, rel=1e-6)
+        assert Fr == pytest.approx(Fr0, rel=1e-6)
+
+
+def test_step_timing_scope(sp):
+    """With timing on, every sparkling_step is also timed as one STEP scope
+    that holds its launches (pack, attraction, repulsion, combine,
+    projection)."""
+    p = inputs.make_problem("tiny")
+    pr = proj_of(p.proj, sp)
+    c = sp.sparkling_create(0)
+    try:
+        g = sp.make_grid(dev(p.grid.rho), p.grid.lo, p.grid.hi, p.grid.n)
+        Kd = dev(p.K)
+        sp.sparkling_step(c, Kd, p.Nc, p.Ns, g, p.eta, pr)          # tuning outside the timing
+        sp.sparkling_status(c)
+        sp.sparkling_set_timing(c, True)
+        sp.sparkling_kernel_times(c, reset=True)
+        for _ in range(3):
+            sp.sparkling_step(c, Kd, p.Nc, p.Ns, g, p.eta, pr)
+        sp.sparkling_status(c)
+        t = sp.sparkling_kernel_times(c, reset=True)
+    finally:
+        c.close()
+    ms, n = t["step"]
+    assert n == 3 and ms > 0
+    inner = sum(t[k][0] for k in ("pack", "attraction", "repulsion", "combine", "project"))
+    assert all(t[k][1] == 3 for k in ("attraction", "repulsion", "project"))
+    assert ms >= 0.9 * inner, (ms, inner)

@@ -1,9 +1,10 @@
 """Every tile shape of the pair kernels, pinned with sparkling_set_shape,
 against the FP64 oracle.
 
-* the three attraction shapes (128 / 256 / 512 threads) and the three shapes
-  of the symmetric repulsion (2 sources per lane with the targets paired in
-  the 64-bit registers, 4 sources per lane, 2 sources per lane with the
+* the three attraction shapes (128 / 256 / 512 threads) and the four shapes
+  of the symmetric repulsion (256 threads: 2 sources per lane with the
+  targets paired in the 64-bit registers, 4 sources per lane, 2 sources per
+  lane with the sources paired; 128 threads with 8 targets per lane and the
   sources paired), on 7,703 samples (8 target tiles, the last ragged) and a
   random density whose rows are not a multiple of 4: A, R, G and the energy,
   plain and regularised kernel;
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 INF = float("inf")
 
-SHAPES = [("attraction", v) for v in range(3)] + [("repulsion", v) for v in range(3)]
+SHAPES = [("attraction", v) for v in range(3)] + [("repulsion", v) for v in range(4)]
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +84,7 @@ def test_pinned_shape_matches_oracle(sp, problem, kernel, variant, eps):
     assert Fr == pytest.approx(Fr0, rel=1e-6)
 
 
-@pytest.mark.parametrize("variant", range(3))
+@pytest.mark.parametrize("variant", range(4))
 def test_batched_step_with_each_repulsion_shape(sp, variant):
     """alpha = beta = inf and a loose box make the projection the identity,
     so G = (K - K') / eta exposes the batched kernels' gradient."""

@@ -1,6 +1,8 @@
-"""Pins of the oracle's fast-repulsion pieces (CPU only): the exact
-short/long split of the repulsion kernel, the cubic B-spline window, and
-the particle-mesh long-range sum against the exact long-range sum."""
+"""CPU checks of the fast-repulsion pieces: pins of the oracle's exact
+short/long split of the repulsion kernel (oracle.repulsion_split), and the
+self-checks of the diagnostic mesh restatement (tests/mesh_reference.py:
+the cubic B-spline window, and its long-range sum against the oracle's exact
+long-range sum)."""
 import math
 
 import numpy as np
@@ -8,7 +10,7 @@ import pytest
 
 import inputs
 import oracle
-from oracle import p3m
+import mesh_reference as p3m
 
 
 def test_bspline_window():
