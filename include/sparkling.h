@@ -348,9 +348,9 @@ SPARKLING_API int sparkling_set_autotune(sparkling_ctx *ctx, int enable);
  * variant 0 = 256 threads per CTA (4 targets per lane), 2 sources per lane,
  * targets paired in the 64-bit registers; 1 = 256 threads, 4 sources per
  * lane, targets paired; 2 = 256 threads, 2 sources per lane, the two sources
- * paired (the shape used where nothing is tuned or pinned, e.g. by the
- * batched step); 3 = 128 threads per CTA (8 targets per lane), 2 sources
- * paired.  variant = -1 unpins (the next call of a new key tunes
+ * paired; 3 = 128 threads per CTA (8 targets per lane), 2 sources paired
+ * (the shape used where nothing is tuned or pinned, e.g. by the batched
+ * step).  variant = -1 unpins (the next call of a new key tunes
  * again when the autotuner is on).  sparkling_set_autotune(ctx, -1) unpins
  * both.  Returns SPARKLING_E_INVAL for another kernel or variant. */
 SPARKLING_API int sparkling_set_shape(sparkling_ctx *ctx, int kernel, int variant);

@@ -194,7 +194,7 @@ cudaError_t launch_combine(const CombineArgs &c, int out_dtype, int sms, cudaStr
 // the targets paired (0, 1) or 2 sources paired (2); 128 threads (8 targets
 // per lane), 2 sources paired (3).
 constexpr int kSymVariants = 4;
-constexpr int kSymDefault = 2;        // shape used where nothing was tuned or pinned
+constexpr int kSymDefault = 3;        // shape used where nothing was tuned or pinned
 int sym_variant_sources(int v);
 bool sym_variant_source_paired(int v);
 int sym_variant_threads(int v);
