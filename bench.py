@@ -299,12 +299,12 @@ def oracle_sample(prob, seconds: float, seed: int = 1, K64=None):
     per_target = P + N - 1
     threads = oracle_threads()
     m = min(N, 4 * threads)
-    for attempt in range(2):
+    for attempt in range(3):
         idx = rng.choice(N, size=m, replace=False)
         t0 = time.perf_counter()
         oracle.forces(K, prob.grid, targets=idx)
         dt = time.perf_counter() - t0
-        if attempt or dt >= 0.8 * seconds or m >= N:
+        if attempt == 2 or dt >= 0.7 * seconds or m >= N:
             break
         m = min(N, max(m, int(m * seconds / max(dt, 1e-6))))
     pairs = m * per_target
