@@ -70,3 +70,36 @@ def test_reference_arm_prints_one_line_on_rank0_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_traffic_figure_only_for_the_kernel_it_was_measured_on(tmp_path, monkeypatch):
+    """The bench line's DRAM traffic comes from the committed ncu summary's
+    fit, only for the density it was measured on and only while the
+    attraction kernel's source hashes to the value recorded there."""
+    import inputs
+    a = bench.parse_args([])
+    p = inputs.make_problem("tiny")
+    prof = tmp_path / "traffic.md"
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
+    assert bench.attraction_traffic(p, a) is None                 # no summary
+    sha = bench.attraction_source_sha()
+    P = int(p.grid.rho.size)
+    prof.write_text(f"traffic-fit: kernel_sha={sha} density={P} bytes_const=1.5e6 "
+                    f"bytes_per_target=100\n")
+    t = bench.attraction_traffic(p, a)
+    assert t["bytes_per_launch"] == pytest.approx(1.5e6 + 100 * p.N)
+    prof.write_text(f"traffic-fit: kernel_sha=0000000000000000 density={P} bytes_const=1.5e6 "
+                    f"bytes_per_target=100\n")
+    assert bench.attraction_traffic(p, a) is None                 # another kernel source
+    prof.write_text(f"traffic-fit: kernel_sha={sha} density={P + 1} bytes_const=1.5e6 "
+                    f"bytes_per_target=100\n")
+    assert bench.attraction_traffic(p, a) is None                 # another density
+    assert bench.attraction_traffic(p, bench.parse_args(["--acc", "fp64pair"])) is None
+
+
+def test_shot_stride_keeps_every_sth_shot():
+    full = bench.load_problem("tiny", 0)
+    sub = bench.load_problem("tiny", 0, 4)
+    assert sub.Nc == (full.Nc + 3) // 4 and sub.Ns == full.Ns
+    K = full.K.reshape(full.Nc, full.Ns, 3)[::4].reshape(-1, 3)
+    assert (sub.K == K).all() and sub.eta == pytest.approx(1.0 / sub.N)
