@@ -67,7 +67,8 @@ struct sparkling_ctx {
         bool valid = false;
         int B = 0, Ns = 0, acc = -1, dtype = -1, ctas = 0, items_per_cta = 0;
         int64_t n_pair_items = 0;
-        std::vector<double> item_pairs;   // pair count of every pair item (tuning prefix)
+        int64_t n_lead_items = 0;         // pair items ahead of the first projection item
+        std::vector<double> item_pairs;   // pair count of every item (0: projection)
         std::vector<int64_t> off;
         std::vector<int32_t> dims;
         std::vector<EngineTraj> traj;
@@ -878,9 +879,16 @@ int64_t pair_cost(int64_t N, int64_t P) { return N * P + N * N; }
 
 // Work list of one batched step: per trajectory and target tile, attraction
 // items (runs of grid rows) and repulsion items (runs of source blocks), each
-// of about total / (ctas * items_per_cta) pairs, then one projection item per
+// of about total / (ctas * items_per_cta) pairs, and one projection item per
 // shot.  Attraction and repulsion items alternate so that neighbouring CTAs
 // (and hence the CTAs resident on one SM) mix SFU-bound and issue-bound work.
+// The projection items of trajectory t are placed once at least 2 * ctas
+// pair items have followed t's last pair item (the rest close the list): by
+// the time a CTA takes one, t's pair items -- dispensed two waves of CTAs
+// earlier -- are done, so it rarely waits, and the projections' FP64 work
+// overlaps later trajectories' pair items.  Every pair item of t still comes
+// before every projection item of t in the list, the order that makes every
+// wait of a projection item end.
 void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
                      const sparkling_grid *grids, int ctas, int items_per_cta, bool sym)
 {
@@ -895,6 +903,19 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
     b.traj.assign(B, EngineTraj());
     b.items.clear();
     b.item_pairs.clear();
+    b.n_pair_items = 0;
+    b.n_lead_items = -1;
+    auto project_items = [&](int t) {
+        if (b.n_lead_items < 0) b.n_lead_items = (int64_t)b.items.size();
+        for (int c = 0; c < b.traj[t].Nc; ++c) {
+            EngineItem it;
+            it.kind = kItemProject; it.traj = t; it.tile = c; it.slot = 0; it.u0 = 0; it.u1 = 0;
+            b.items.push_back(it);
+            b.item_pairs.push_back(0.0);
+        }
+    };
+    std::vector<int64_t> ends;       // pair items placed up to the end of trajectory t
+    int released = 0;                // trajectories whose projection items are placed
     int64_t part = 0;
     for (int t = 0; t < B; ++t) {
         EngineTraj &tr = b.traj[t];
@@ -947,14 +968,12 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
                 }
             }
         }
+        b.n_pair_items += tr.n_pair_items;
+        ends.push_back(b.n_pair_items);
+        while (released < t && b.n_pair_items - ends[released] >= 2 * (int64_t)ctas)
+            project_items(released++);
     }
-    b.n_pair_items = (int64_t)b.items.size();
-    for (int t = 0; t < B; ++t)
-        for (int c = 0; c < b.traj[t].Nc; ++c) {
-            EngineItem it;
-            it.kind = kItemProject; it.traj = t; it.tile = c; it.slot = 0; it.u0 = 0; it.u1 = 0;
-            b.items.push_back(it);
-        }
+    while (released < B) project_items(released++);
 }
 
 int validate_batch(sparkling_ctx *ctx, int32_t B, const int64_t *off, const void *K, int K_dtype,
@@ -1068,7 +1087,9 @@ int tune_engine(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_grid *
     if ((s = batch_pack(ctx, K, K_dtype, grids, st))) return s;
     int64_t n = 0;
     double pairs = 0.0;
-    while (n < b.n_pair_items && pairs < 1.5e11) pairs += b.item_pairs[n++];
+    // a prefix of pair items only (they write partial slots and counters,
+    // which the real step resets and overwrites; K is untouched)
+    while (n < b.n_lead_items && pairs < 1.5e11) pairs += b.item_pairs[n++];
     cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
     int best = 0;
     double best_rate = 0.0;
