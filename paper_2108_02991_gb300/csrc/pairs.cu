@@ -84,9 +84,10 @@ __global__ void pack_grid_kernel(const float *__restrict__ rho, int nx, int ny, 
         atomicOr(status, kDevNonFinite);
 }
 
-// Resident CTAs the launch bounds ask for: 768 threads per SM at 128/256
-// threads per CTA (registers <= 80), 1024 at 512 (registers <= 64).
-constexpr int min_ctas(int nt) { return nt >= 512 ? 2 : 768 / nt; }
+// Resident CTAs the launch bounds ask for: three at 128 or 256 threads per
+// CTA (shared memory holds no more: registers <= 168 and <= 80), two at 512
+// (registers <= 64).
+constexpr int min_ctas(int nt) { return nt >= 512 ? 2 : 3; }
 
 template <int ACC, bool ENERGY, int NT>
 __global__ void __launch_bounds__(NT, min_ctas(NT)) attraction_kernel(const AttrArgs a)
