@@ -65,6 +65,9 @@ def parse_args(argv=None):
     ap.add_argument("--acc", choices=("kahan", "fp64", "fp64pair"), default="kahan",
                     help="per-target accumulation: compensated FP32 folds, FP64 folds, or the "
                          "plain FP64-accumulate form (every attraction pair term added in FP64)")
+    ap.add_argument("--two-launches", action="store_true",
+                    help="batched step: the symmetric repulsion in its own kernel ahead of the "
+                         "engine instead of as items of the engine's work list (one launch)")
     ap.add_argument("--projection", choices=("fp64", "mixed"), default="fp64",
                     help="projection arithmetic: FP64 duals (default) or the opt-in mixed form")
     ap.add_argument("--shot-stride", type=int, default=1,
@@ -375,6 +378,7 @@ class Workload:
         else:
             self.probs = [load_problem(args.workload, seed, args.shot_stride)]
         self.batched = args.workload == "batched" or args.path == "engine"
+        self.one_launch = not args.two_launches
         self.off = [0]
         for p in self.probs:
             self.off.append(self.off[-1] + p.N)
@@ -409,7 +413,8 @@ class Workload:
         sp = self.sp
         if self.batched:
             sp.sparkling_step_batched(self.ctx, self.K, self.off, self.Ns, self.grids, self.etas,
-                                      self.projs, self.acc, graph=True)
+                                      self.projs, self.acc, graph=True,
+                                      one_launch=self.one_launch)
         else:
             p = self.probs[0]
             sp.sparkling_step(self.ctx, self.K, p.Nc, p.Ns, self.grids[0], p.eta, self.projs[0],
@@ -642,7 +647,9 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": w.desc, "N": w.N, "P": int(p0.grid.rho.size),
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
-                       "n_pit": p0.proj.n_iter, "path": "engine" if w.batched else "kernels",
+                       "n_pit": p0.proj.n_iter,
+                       "path": ("engine, one launch" if w.one_launch else "engine")
+                       if w.batched else "kernels",
                        "l2": "flushed (512 MB write) before every step", "acc": args.acc,
                        "projection": args.projection,
                        "attraction": args.attraction, "repulsion": args.repulsion,

@@ -158,6 +158,7 @@ typedef struct sparkling_mesh {
 
 /* Flags of sparkling_step_batched. */
 #define SPARKLING_BATCH_GRAPH 1     /* replay the step from a cached CUDA graph */
+#define SPARKLING_BATCH_TWO_LAUNCHES 2 /* the symmetric repulsion in its own kernel first */
 
 /* Step schedule of the multi-resolution driver (Algorithm 1 and Sec. II-C,
  * choice of step size). */
@@ -245,14 +246,19 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
                                  const sparkling_proj *proj, void *stream);
 
 /* One projected-gradient step K_b <- Pi(K_b - eta_b G(K_b)) for B
- * independent trajectories of uneven size in two launches (plus the packing
- * of samples and densities): the symmetric repulsion of every trajectory
- * (each unordered pair once, exact fixed-point totals), then one persistent
- * kernel that runs a work list of attraction items (a tile of 1024 targets
- * against a run of grid rows) followed by one projection item per shot that
- * waits (bounded) for its trajectory's attraction items.  (Where the
- * symmetric kernel cannot be resident the repulsion runs as directed items
- * of the same work list.)  Same arithmetic as sparkling_step: FP32 pairs,
+ * independent trajectories of uneven size in one persistent launch (plus
+ * the packing of samples and densities): a work list of attraction items (a
+ * tile of 1024 targets against a run of grid rows) and symmetric repulsion
+ * items (a tile of targets against a run of source tiles, each unordered
+ * pair once, exact fixed-point totals per sample), followed by one
+ * projection item per shot that waits (bounded) for its trajectory's pair
+ * items.  With SPARKLING_BATCH_TWO_LAUNCHES (and wherever the one-launch
+ * kernel shape cannot be resident) the symmetric repulsion of every
+ * trajectory runs first in its own kernel -- the same totals bit for bit --
+ * and the persistent kernel's list holds only the attraction and projection
+ * items.  (Where the symmetric kernel cannot be resident either, the
+ * repulsion runs as directed items of the work list.)  Same arithmetic as
+ * sparkling_step: FP32 pairs,
  * acc per-target folds, FP64 gradient, step and projection (fixed n_iter;
  * converged mode is not available here); the context's regularisation
  * applies, its attraction and repulsion modes do not (direct sums).
@@ -265,7 +271,9 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
  *   flags     SPARKLING_BATCH_GRAPH: from the second call with the same
  *             shapes, K, densities and workspace on, the device work of the
  *             step is captured once into a CUDA graph and replayed (calls on
- *             a stream the caller is itself capturing are never captured).
+ *             a stream the caller is itself capturing are never captured);
+ *             SPARKLING_BATCH_TWO_LAUNCHES: the repulsion kernel ahead of
+ *             the persistent kernel, as above.
  * The work list is planned and uploaded when the shapes change; make the
  * first call of a shape outside any caller-side stream capture.  The item
  * granularity comes from the context's autotuned setting.  Asynchronous. */

@@ -21,6 +21,7 @@ ACC_KAHAN32, ACC_FP64, ACC_FP64_PAIR = 0, 1, 2
 KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine", "driver", "step")
 PROJECTION_FP64, PROJECTION_MIXED = 0, 1
 BATCH_GRAPH = 1
+BATCH_TWO_LAUNCHES = 2
 ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
 REPULSION_DIRECT, REPULSION_MESH = 0, 1
 
@@ -324,9 +325,11 @@ def sparkling_step(ctx: Context, K, Nc: int, Ns: int, grid: Grid, eta: float, pr
 
 def sparkling_step_batched(ctx: Context, K, traj_off: Sequence[int], Ns: int,
                            grids: Sequence[Grid], etas: Sequence[float], projs: Sequence[Proj],
-                           acc: int = ACC_KAHAN32, graph: bool = True, stream=None):
+                           acc: int = ACC_KAHAN32, graph: bool = True, one_launch: bool = True,
+                           stream=None):
     """One projected-gradient step of B trajectories (samples
-    [traj_off[b], traj_off[b+1]) of K) in one persistent launch, in place."""
+    [traj_off[b], traj_off[b+1]) of K), in place, in one persistent launch;
+    one_launch=False runs the symmetric repulsion in its own kernel first."""
     B = len(grids)
     if len(traj_off) != B + 1 or len(etas) != B or len(projs) != B:
         raise ValueError("traj_off needs B+1 entries, etas and projs B")
@@ -336,7 +339,9 @@ def sparkling_step_batched(ctx: Context, K, traj_off: Sequence[int], Ns: int,
     parr = (Proj * B)(*projs)
     _check(ctx, lib().sparkling_step_batched(ctx.handle, B, off, _dev_ptr(K, "K"), _dtype_code(K),
                                              int(Ns), garr, earr, parr, acc,
-                                             BATCH_GRAPH if graph else 0, _stream(stream)))
+                                             (BATCH_GRAPH if graph else 0) |
+                                             (0 if one_launch else BATCH_TWO_LAUNCHES),
+                                             _stream(stream)))
 
 
 def sparkling_step_host(ctx: Context, K_host, Nc: int, Ns: int, grid: Grid, rho_host, eta: float,

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparkling.so")
 SOURCES = ["api.cu", "pairs.cu", "repulsion.cu", "repulsion_sym.cu", "project.cu", "noalloc.cu",
            "engine.cu", "field.cu", "driver.cu", "mesh.cu"]
-HEADERS = ["kernels.h", "ptx.cuh", "pair_dev.cuh", "project_dev.cuh"]
+HEADERS = ["kernels.h", "ptx.cuh", "pair_dev.cuh", "project_dev.cuh", "sym_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

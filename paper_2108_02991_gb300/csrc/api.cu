@@ -76,6 +76,7 @@ struct sparkling_ctx {
         std::vector<size_t> o_rho, o_coords;
         size_t o_pos = 0, o_traj = 0, o_items = 0, o_cnt = 0, o_part = 0, o_gstate = 0, end = 0;
         bool sym = false;                 // repulsion by the batched symmetric kernel
+        bool one_launch = false;          // symmetric repulsion items in the engine's work list
         size_t o_racc = 0, o_symtraj = 0;
         int64_t sym_units = 0;
         std::vector<SymTraj> symtraj;
@@ -878,10 +879,13 @@ namespace {
 int64_t pair_cost(int64_t N, int64_t P) { return N * P + N * N; }
 
 // Work list of one batched step: per trajectory and target tile, attraction
-// items (runs of grid rows) and repulsion items (runs of source blocks), each
-// of about total / (ctas * items_per_cta) pairs, and one projection item per
-// shot.  Attraction and repulsion items alternate so that neighbouring CTAs
-// (and hence the CTAs resident on one SM) mix SFU-bound and issue-bound work.
+// items (runs of grid rows) and repulsion items -- runs of source blocks
+// (directed), or, in the one-launch shape, runs of source tiles J >= the
+// target tile (symmetric) -- each of about total / (ctas * items_per_cta)
+// pairs, and one projection item per shot.  With `sym` the repulsion runs in
+// a separate kernel and the list holds no repulsion items.  Attraction and
+// repulsion items alternate so that neighbouring CTAs (and hence the CTAs
+// resident on one SM) mix SFU-bound and FP32-bound work.
 // The projection items of trajectory t are placed once at least 2 * ctas
 // pair items have followed t's last pair item (the rest close the list): by
 // the time a CTA takes one, t's pair items -- dispensed two waves of CTAs
@@ -890,7 +894,8 @@ int64_t pair_cost(int64_t N, int64_t P) { return N * P + N * N; }
 // before every projection item of t in the list, the order that makes every
 // wait of a projection item end.
 void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
-                     const sparkling_grid *grids, int ctas, int items_per_cta, bool sym)
+                     const sparkling_grid *grids, int ctas, int items_per_cta, bool sym,
+                     bool one_launch)
 {
     const int B = (int)off.size() - 1;
     int64_t total = 0;
@@ -929,7 +934,11 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
         int64_t sc = (int64_t)(target / ((double)kTile * kSrcBlock) + 0.5);
         sc = sc < 1 ? 1 : (sc > blocks ? blocks : sc);
         const int ach = (int)((rows + rc - 1) / rc);
-        const int rch = sym ? 0 : (int)((blocks + sc - 1) / sc);   // sym: a separate kernel
+        const int rch = sym || one_launch ? 0 : (int)((blocks + sc - 1) / sc);
+        // symmetric items: runs of up to L source tiles (a tile pair is
+        // about 2 * kTile^2 directed pairs)
+        int64_t L = (int64_t)(target / (2.0 * kTile * kTile) + 0.5);
+        L = L < 1 ? 1 : (L > 64 ? 64 : L);
         tr.off = off[t];
         tr.N = N;
         tr.Ns = b.Ns;
@@ -942,10 +951,13 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
         tr.part_off = part * kTile;
         part += (int64_t)tr.tiles * tr.slots;
         tr.n_pair_items = tr.tiles * tr.slots;
+        auto count_of = [&](int64_t J) { return (double)std::min<int64_t>(kTile, N - J * kTile); };
         for (int64_t tile = 0; tile < tr.tiles; ++tile) {
             int ia = 0, ir = 0;
-            while (ia < ach || ir < rch) {
-                const double tgt = (double)std::min<int64_t>(kTile, N - tile * kTile);
+            const int64_t nsr = one_launch ? (tr.tiles - tile + L - 1) / L : 0;
+            int64_t is = 0;
+            while (ia < ach || ir < rch || is < nsr) {
+                const double tgt = count_of(tile);
                 if (ia < ach) {
                     EngineItem it;
                     it.kind = kItemAttraction; it.traj = t; it.tile = (int32_t)tile; it.slot = ia;
@@ -965,6 +977,19 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
                     b.item_pairs.push_back(tgt * (double)(std::min<int64_t>(it.u1 * kSrcBlock, N) -
                                                           it.u0 * kSrcBlock));
                     ++ir;
+                }
+                if (is < nsr) {
+                    EngineItem it;
+                    it.kind = kItemSym; it.traj = t; it.tile = (int32_t)tile; it.slot = 0;
+                    it.u0 = tile + is * L;
+                    it.u1 = std::min<int64_t>(it.u0 + L, tr.tiles);
+                    double pairs = 0.0;   // directed: the diagonal pair once, the others twice
+                    for (int64_t J = it.u0; J < it.u1; ++J)
+                        pairs += (J == tile ? 1.0 : 2.0) * tgt * count_of(J);
+                    b.items.push_back(it);
+                    b.item_pairs.push_back(pairs);
+                    ++tr.n_pair_items;
+                    ++is;
                 }
             }
         }
@@ -1042,7 +1067,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
     e.status = ctx->d_status;
     e.eps2 = eps2_of(ctx);
-    e.racc = b.sym ? at<unsigned long long>(ctx, b.o_racc) : nullptr;
+    e.racc = b.sym || b.one_launch ? at<unsigned long long>(ctx, b.o_racc) : nullptr;
     const int ctas = ctx->sms * engine_ctas_per_sm(acc, K_dtype, variant);
     CK(launch_engine(e, acc, K_dtype, variant, std::min(ctas, b.ctas), st));
     return SPARKLING_OK;
@@ -1072,6 +1097,10 @@ int batch_device_work(sparkling_ctx *ctx, void *K, int K_dtype, const sparkling_
         const int sv = ctx->sym_choice < 0 ? kSymDefault : ctx->sym_choice;
         sa.ctas = std::min<int64_t>((int64_t)ctx->sms * ctx->occ_sym[0][sv], b.sym_units);
         CK(launch_repulsion_sym(sa, false, sv, st));
+    } else if (b.one_launch) {
+        // the engine's symmetric items add into these totals
+        CK(cudaMemsetAsync(at<unsigned long long>(ctx, b.o_racc), 0,
+                           (size_t)b.off[b.B] * 3 * sizeof(unsigned long long), st));
     }
     return batch_engine(ctx, K, K_dtype, acc, variant, (int64_t)b.items.size(), st);
 }
@@ -1494,22 +1523,33 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
     std::vector<int32_t> dims;
     for (int t = 0; t < B; ++t)
         for (int a = 0; a < 3; ++a) dims.push_back(grids[t].n[a]);
+    // one launch (the default): the symmetric repulsion as items of the
+    // engine's work list; it needs the symmetric arithmetic and the one-launch
+    // shape to be resident, else the repulsion runs ahead in its own kernel
+    const bool one_launch = !(flags & SPARKLING_BATCH_TWO_LAUNCHES) && ctx->rep_symmetric &&
+                            engine_ctas_per_sm(acc, K_dtype, kEngineOneLaunch) >= 1;
+    cudaGetLastError();
     int occ = 0;
-    for (int v = 0; v < kEngineVariants; ++v) occ = std::max(occ, engine_ctas_per_sm(acc, K_dtype, v));
+    if (one_launch)
+        occ = engine_ctas_per_sm(acc, K_dtype, kEngineOneLaunch);
+    else
+        for (int v = 0; v < kEngineVariants; ++v)
+            occ = std::max(occ, engine_ctas_per_sm(acc, K_dtype, v));
     cudaGetLastError();
     if (occ < 1) return fail(ctx, SPARKLING_E_CUDA, "engine kernel cannot be resident");
     const int ctas = ctx->sms * occ;   // the largest wave of any engine shape
     const bool same = b.valid && b.B == B && b.Ns == Ns && b.acc == acc && b.dtype == K_dtype &&
                       b.ctas == ctas && b.items_per_cta == ctx->items_per_cta && b.off == off &&
-                      b.dims == dims;
+                      b.dims == dims && b.one_launch == one_launch;
     if (!same) {
         if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
         b = sparkling_ctx::Batch();
         b.B = B; b.Ns = Ns; b.acc = acc; b.dtype = K_dtype; b.ctas = ctas;
         b.items_per_cta = ctx->items_per_cta;
         b.off = off; b.dims = dims;
-        b.sym = ctx->rep_symmetric;
-        build_work_list(b, off, grids, ctas, ctx->items_per_cta, b.sym);
+        b.one_launch = one_launch;
+        b.sym = ctx->rep_symmetric && !one_launch;
+        build_work_list(b, off, grids, ctas, ctx->items_per_cta, b.sym, b.one_launch);
         Carve cv;
         b.o_pos = cv.take((size_t)off[B] * sizeof(float4));
         for (int t = 0; t < B; ++t) {
@@ -1524,8 +1564,9 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         b.o_part = cv.take((size_t)parts * kTile * sizeof(dacc4));
         b.proj_in_smem = project_state_bytes(Ns) <= engine_proj_smem_limit();
         if (!b.proj_in_smem) b.o_gstate = cv.take((size_t)ctas * project_state_bytes(Ns));
-        if (b.sym) {
+        if (b.sym || b.one_launch)
             b.o_racc = cv.take((size_t)off[B] * 3 * sizeof(unsigned long long));
+        if (b.sym) {
             b.o_symtraj = cv.take((size_t)B * sizeof(SymTraj));
             int64_t u = 0;
             for (int t = 0; t < B; ++t) {
@@ -1580,9 +1621,11 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cap));
-    if (ctx->autotune && ctx->engine_choice[acc][K_dtype] < 0 && cap == cudaStreamCaptureStatusNone)
+    if (!b.one_launch && ctx->autotune && ctx->engine_choice[acc][K_dtype] < 0 &&
+        cap == cudaStreamCaptureStatusNone)
         if ((s = tune_engine(ctx, K, K_dtype, grids, acc, st))) return s;
-    const int variant = ctx->engine_choice[acc][K_dtype] < 0 ? 0 : ctx->engine_choice[acc][K_dtype];
+    const int variant = b.one_launch ? kEngineOneLaunch
+                        : ctx->engine_choice[acc][K_dtype] < 0 ? 0 : ctx->engine_choice[acc][K_dtype];
 
     // Graph replay when asked for and the call matches the captured one.
     std::vector<const void *> key;

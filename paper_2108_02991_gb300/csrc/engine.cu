@@ -5,11 +5,13 @@
 // The host builds a work list (api.cu): for every trajectory and every tile
 // of 1024 targets, attraction items (a run of grid rows), then one
 // projection item per shot.  The repulsion of every trajectory is summed
-// before the launch by the batched symmetric kernel (exact fixed-point
-// totals per sample, read through EngineArgs::racc); contexts where that
-// kernel cannot be resident get directed repulsion items (a run of source
-// blocks) interleaved with the attraction items instead.  Every CTA of a
-// single wave pulls the next item from a global counter.
+// with each unordered pair once, into exact fixed-point totals per sample
+// (EngineArgs::racc): in the one-launch shape by symmetric repulsion items
+// of the same work list (a target tile against a run of source tiles),
+// otherwise by the batched symmetric kernel before the launch; contexts
+// where that kernel cannot be resident get directed repulsion items (a run
+// of source blocks) interleaved with the attraction items instead.  Every
+// CTA of a single wave pulls the next item from a global counter.
 //
 // A pair item writes the FP64 partial sums of its tile into its own slot and
 // then bumps its trajectory's completion counter.  A projection item waits
@@ -29,6 +31,7 @@
 #include "pair_dev.cuh"
 #include "project_dev.cuh"
 #include "ptx.cuh"
+#include "sym_dev.cuh"
 
 namespace sparkling {
 
@@ -153,7 +156,7 @@ __device__ __noinline__ bool project_item(const EngineArgs &e, const EngineItem 
             if (s < ach) { g[0] += xy.x; g[1] += xy.y; g[2] += zz; }
             else { r[0] += xy.x; r[1] += xy.y; r[2] += zz; }
         }
-        if (e.racc) {   // symmetric repulsion totals (fixed point), written before the launch
+        if (e.racc) {   // symmetric repulsion totals (fixed point), complete once the pair items are
             const unsigned long long *q = e.racc + 3 * (tr.off + i);
             for (int c = 0; c < 3; ++c) r[c] = (double)(long long)__ldcg(q + c) / kFixScale;
         }
@@ -171,10 +174,95 @@ __device__ __noinline__ bool project_item(const EngineArgs &e, const EngineItem 
     return true;
 }
 
+// A symmetric repulsion item: the tile pairs (I, J), J in [J0, J1), of one
+// trajectory (I <= J0), the J tiles streamed through the stage buffers by
+// bulk copies.  Each pair's source sums (jacc, shared) and target sums are
+// added to the fixed-point totals e.racc with 64-bit atomics -- the
+// integers of the standalone kernel, so the totals are the same bit for bit.
+template <int NT>
+__device__ bool sym_item_run(const EngineArgs &e, const EngineTraj &tr, int64_t I, int64_t J0,
+                             int64_t J1, float4 *stage, uint64_t *bars, float *jacc,
+                             uint32_t &consumed)
+{
+    constexpr int T = kTile / NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float4 *pos = e.pos + tr.off;
+    unsigned long long *acc = e.racc + 3 * tr.off;
+    const int64_t N = tr.N;
+    const uint32_t n = (uint32_t)(J1 - J0);
+    auto count_of = [&](int64_t J) {
+        const int64_t rem = N - J * kTile;
+        return rem < kTile ? (int)rem : kTile;
+    };
+    auto issue = [&](uint32_t s) {
+        const uint32_t g = consumed + s;
+        const int64_t J = J0 + s;
+        bulk_load(stage + (g % kStages) * kTile, pos + J * kTile,
+                  (uint32_t)(count_of(J) * sizeof(float4)), &bars[g % kStages]);
+    };
+    if (tid == 0) {
+        fence_proxy_async_smem();     // the buffers last held generic-proxy data
+        for (uint32_t s = 0; s < n && s < (uint32_t)kStages; ++s) issue(s);
+    }
+    // the thread's targets l = warp*32T + t*32 + lane of tile I
+    float tx[T], ty[T], tz[T], tm[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t i = I * kTile + warp * 32 * T + t * 32 + lane;
+        const bool ok = i < N;
+        const float4 p = ok ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[t] = p.x; ty[t] = p.y; tz[t] = p.z; tm[t] = ok ? 1.f : 0.f;
+    }
+    for (uint32_t s = 0; s < n; ++s) {
+        const uint32_t g = consumed + s;
+        const bool ok = mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1, e.status);
+        if (__syncthreads_or(!ok)) {
+            const uint32_t left = n - s;
+            drain_stages(bars, g, left < (uint32_t)kStages ? left : (uint32_t)kStages, e.status);
+            return false;
+        }
+        const float4 *src = stage + (g % kStages) * kTile;
+        const int64_t J = J0 + s;
+        const int jvalid = count_of(J);
+        float ai[T][3];
+#pragma unroll
+        for (int t = 0; t < T; ++t) ai[t][0] = ai[t][1] = ai[t][2] = 0.f;
+        if (J == I) {
+            diag_item<false, NT>(src, jvalid, tx, ty, tz, e.eps2, ai);
+        } else {
+            for (int q = tid; q < 3 * kTile; q += NT) jacc[q] = 0.f;
+            __syncthreads();
+            if (jvalid < kTile)
+                sym_item_sp<false, true, NT>(src, jvalid, tx, ty, tz, tm, e.eps2, ai, jacc);
+            else
+                sym_item_sp<false, false, NT>(src, jvalid, tx, ty, tz, tm, e.eps2, ai, jacc);
+            for (int l = tid; l < jvalid; l += NT)
+#pragma unroll
+                for (int v = 0; v < 3; ++v)
+                    add_fix(&acc[(J * kTile + l) * 3 + v], to_fix(jacc[v * kTile + l]));
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = I * kTile + warp * 32 * T + t * 32 + lane;
+            if (i < N)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) add_fix(&acc[i * 3 + v], to_fix(ai[t][v]));
+        }
+        __syncthreads();   // this stage and jacc are free again
+        if (tid == 0 && s + kStages < n) {
+            fence_proxy_async_smem();
+            issue(s + kStages);
+        }
+    }
+    consumed += n;
+    return true;
+}
+
 // REP: the work list may hold directed repulsion items (only when the
 // batched symmetric kernel cannot run); without them the kernel carries no
-// repulsion code.
-template <int ACC, typename KT, int NT, bool REP>
+// repulsion code.  SYM: the one-launch shape, whose work list holds the
+// symmetric repulsion items.
+template <int ACC, typename KT, int NT, bool REP, bool SYM>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const EngineArgs e)
 {
     extern __shared__ __align__(128) unsigned char esm[];
@@ -206,6 +294,12 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
                                                 bars, accbase, consumed))
                 return;
             mark_done(e.done + item.traj);
+        } else if (SYM && item.kind == kItemSym) {
+            if (!sym_item_run<NT>(e, tr, item.tile, item.u0, item.u1,
+                                  reinterpret_cast<float4 *>(stage), bars,
+                                  static_cast<float *>(accbase), consumed))
+                return;
+            mark_done(e.done + item.traj);
         } else if (REP && item.kind == kItemRepulsion) {
             const RepArgs r = rep_args(tr, e);
             if (!repulsion_segment<ACC, false, NT, (NT >= 512 ? 2 : 4)>(r, item.tile, item.u0, item.u1, item.slot,
@@ -220,21 +314,27 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
     }
 }
 
-template <int ACC, typename KT, int NT, bool REP>
-void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT, NT, REP>); }
+template <int ACC, typename KT, int NT, bool REP, bool SYM>
+void *engine_fn() { return reinterpret_cast<void *>(engine_kernel<ACC, KT, NT, REP, SYM>); }
 
-template <int NT, bool REP>
+template <int NT, bool REP, bool SYM>
 void *pick_engine_nt(int acc, int dtype)
 {
-    if (acc == 0) return dtype == 0 ? engine_fn<0, float, NT, REP>() : engine_fn<0, double, NT, REP>();
-    return dtype == 0 ? engine_fn<1, float, NT, REP>() : engine_fn<1, double, NT, REP>();
+    if (acc == 0)
+        return dtype == 0 ? engine_fn<0, float, NT, REP, SYM>() : engine_fn<0, double, NT, REP, SYM>();
+    return dtype == 0 ? engine_fn<1, float, NT, REP, SYM>() : engine_fn<1, double, NT, REP, SYM>();
 }
 
+// rep: directed repulsion items (not in the one-launch shape, which has the
+// symmetric items instead)
 void *pick_engine(int acc, int dtype, int variant, bool rep)
 {
+    if (variant == kEngineOneLaunch) return pick_engine_nt<128, false, true>(acc, dtype);
     if (rep)
-        return variant == 1 ? pick_engine_nt<512, true>(acc, dtype) : pick_engine_nt<256, true>(acc, dtype);
-    return variant == 1 ? pick_engine_nt<512, false>(acc, dtype) : pick_engine_nt<256, false>(acc, dtype);
+        return variant == 1 ? pick_engine_nt<512, true, false>(acc, dtype)
+                            : pick_engine_nt<256, true, false>(acc, dtype);
+    return variant == 1 ? pick_engine_nt<512, false, false>(acc, dtype)
+                        : pick_engine_nt<256, false, false>(acc, dtype);
 }
 
 } // namespace
@@ -243,12 +343,12 @@ size_t engine_smem_bytes() { return kHeadBytes + kUnionBytes; }
 
 size_t engine_proj_smem_limit() { return kUnionBytes; }
 
-int engine_variant_threads(int v) { return v == 1 ? 512 : 256; }
+int engine_variant_threads(int v) { return v == kEngineOneLaunch ? 128 : v == 1 ? 512 : 256; }
 
 int engine_ctas_per_sm(int acc, int dtype, int variant)
 {
     int best = 1 << 30;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < (variant == kEngineOneLaunch ? 1 : 2); ++rep) {
         void *fn = pick_engine(acc, dtype, variant, rep != 0);
         const size_t smem = engine_smem_bytes();
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

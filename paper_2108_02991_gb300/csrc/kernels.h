@@ -259,7 +259,8 @@ cudaError_t launch_project(const ProjArgs &p, int dtype, int grid, cudaStream_t 
 
 // Persistent engine (engine.cu): one launch runs a work list of pair items
 // (attraction or repulsion of one target tile against a run of grid rows or
-// source blocks) for any number of trajectories, followed by per-shot
+// source blocks, or symmetric repulsion of one target tile against a run of
+// source tiles) for any number of trajectories, followed by per-shot
 // projection items that wait until their trajectory's pair items are done.
 struct EngineTraj {
     int64_t off;             // first sample of the trajectory in K / pos
@@ -279,12 +280,12 @@ struct EngineTraj {
     int32_t pin_index, n_iter;
 };
 
-constexpr int kItemAttraction = 0, kItemRepulsion = 1, kItemProject = 2;
+constexpr int kItemAttraction = 0, kItemRepulsion = 1, kItemProject = 2, kItemSym = 3;
 
 struct EngineItem {
     int32_t kind, traj;
     int32_t tile, slot;      // pair items: target tile and partial slot; project: shot, -
-    int64_t u0, u1;          // pair items: grid-row or source-block range
+    int64_t u0, u1;          // pair items: grid-row or source-block range; sym: source tiles
 };
 
 struct EngineArgs {
@@ -299,7 +300,7 @@ struct EngineArgs {
     unsigned int *queue;     // next item (reset to 0 before every launch)
     unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
     double *gstate;          // per-CTA projection state when it is not in shared memory
-    const unsigned long long *racc = nullptr;   // symmetric repulsion sums [sum N][3], or null
+    unsigned long long *racc = nullptr;   // symmetric repulsion sums [sum N][3], or null
     float eps2 = kEps2;      // eps^2 (>= kEps2) added to every r^2
     int *status;
 };
@@ -307,6 +308,9 @@ struct EngineArgs {
 size_t engine_smem_bytes();
 size_t engine_proj_smem_limit();     // largest 18*Ns*8 that fits the shared-memory union
 constexpr int kEngineVariants = 2;    // threads 256 (repulsion unroll 4) / 512 (unroll 2)
+// The one-launch shape: 128 threads (8 targets per thread, three CTAs per
+// SM), whose work list also holds the symmetric repulsion (kItemSym items).
+constexpr int kEngineOneLaunch = 2;
 int engine_variant_threads(int v);
 int engine_ctas_per_sm(int acc, int dtype, int variant);
 cudaError_t launch_engine(const EngineArgs &e, int acc, int dtype, int variant, int ctas,

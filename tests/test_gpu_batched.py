@@ -1,5 +1,7 @@
-"""The batched persistent step (one engine launch for B trajectories of
-uneven size, optionally replayed from a CUDA graph) against the oracle."""
+"""The batched persistent step (B trajectories of uneven size: one engine
+launch whose work list also holds the symmetric repulsion items -- the
+default -- or the symmetric repulsion kernel followed by the engine;
+optionally replayed from a CUDA graph) against the oracle."""
 import numpy as np
 import pytest
 
@@ -47,7 +49,7 @@ def make_batch(seed, shots, Ns, grid_shapes, dtype):
     return Ks, grids, projs, etas
 
 
-def run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph, calls=1):
+def run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph, calls=1, one_launch=True):
     off = np.concatenate([[0], np.cumsum([k.shape[0] for k in Ks])])
     K = torch.from_numpy(np.concatenate(Ks)).cuda()
     rhos = [torch.from_numpy(g.rho).cuda() for g in grids]
@@ -55,7 +57,7 @@ def run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph, calls=1):
     ps = [sp.make_proj(p.alpha, p.beta, p.box, p.n_iter, p.pin_index, p.pin) for p in projs]
     outs = []
     for _ in range(calls):
-        sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=graph)
+        sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=graph, one_launch=one_launch)
         sp.sparkling_status(ctx)
         outs.append(K.cpu().numpy().copy())
     return off, outs
@@ -66,9 +68,10 @@ def oracle_step(K, g, p, eta, Ns):
                        p.n_iter)
 
 
+@pytest.mark.parametrize("one_launch", [False, True])
 @pytest.mark.parametrize("dtype,mixed", [(np.float64, False), (np.float32, False),
                                          (np.float32, True)])
-def test_batched_step_matches_oracle_every_sample(sp, dtype, mixed):
+def test_batched_step_matches_oracle_every_sample(sp, dtype, mixed, one_launch):
     """Five trajectories (1..21 shots of 64 samples, ragged tiles), grids of
     different shapes (rows not a multiple of 4, a one-cell grid), per-
     trajectory alpha, beta, eta and pins; one eager call.  FP32 samples with
@@ -81,7 +84,8 @@ def test_batched_step_matches_oracle_every_sample(sp, dtype, mixed):
     try:
         if mixed:
             sp.sparkling_set_projection(c, sp.PROJECTION_MIXED)
-        off, outs = run_batched(sp, c, Ks, grids, projs, etas, Ns, graph=False)
+        off, outs = run_batched(sp, c, Ks, grids, projs, etas, Ns, graph=False,
+                                one_launch=one_launch)
     finally:
         c.close()
     out = outs[0]
@@ -99,7 +103,8 @@ def test_batched_step_matches_oracle_every_sample(sp, dtype, mixed):
         np.testing.assert_allclose(got, want, rtol=0, atol=tol)
 
 
-def test_batched_gradient_recovered_from_unconstrained_step(sp, ctx):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batched_gradient_recovered_from_unconstrained_step(sp, ctx, one_launch):
     """With alpha = beta = inf and a loose box the projection is the identity,
     so K' = K - eta G exposes the engine's gradient: G = (K - K') / eta."""
     Ns = 128
@@ -108,23 +113,27 @@ def test_batched_gradient_recovered_from_unconstrained_step(sp, ctx):
     Ks, grids, projs, _ = make_batch(2, shots, Ns, shapes, np.float64)
     projs = [inputs.Proj(INF, INF, 10.0, n_iter=3) for _ in projs]
     etas = [1.0, 0.5, 2.0]
-    off, outs = run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph=False)
+    off, outs = run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph=False,
+                            one_launch=one_launch)
     for b in range(3):
         G = (Ks[b] - outs[0][off[b]:off[b + 1]]) / etas[b]
         _, _, G0 = oracle.forces(Ks[b], grids[b])
         assert_grad_close(G, G0, f"engine G of trajectory {b}")
 
 
-def test_batched_graph_replay_is_bitwise_the_eager_step(sp, ctx):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batched_graph_replay_is_bitwise_the_eager_step(sp, ctx, one_launch):
     """Call 1 runs eagerly, call 2 captures the device work into a CUDA graph,
     call 3 replays it; each matches an eager chain bit for bit."""
     Ns = 64
     Ks, grids, projs, etas = make_batch(3, [4, 6, 3], Ns, [(8, 8, 8), (6, 5, 4), (10, 3, 3)],
                                         np.float32)
-    _, eager = run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph=False, calls=3)
+    _, eager = run_batched(sp, ctx, Ks, grids, projs, etas, Ns, graph=False, calls=3,
+                           one_launch=one_launch)
     ctx2 = sp.sparkling_create(0)
     try:
-        _, graphed = run_batched(sp, ctx2, Ks, grids, projs, etas, Ns, graph=True, calls=3)
+        _, graphed = run_batched(sp, ctx2, Ks, grids, projs, etas, Ns, graph=True, calls=3,
+                                 one_launch=one_launch)
     finally:
         ctx2.close()
     for a, b in zip(eager, graphed):
@@ -166,10 +175,12 @@ def test_batched_workload_sampled(sp, ctx):
                                        atol=PROJ_F32_ROUND + 4 * p.eta * GRAD_ABS)
 
 
-def test_batched_workload_gradient(sp, ctx):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batched_workload_gradient(sp, ctx, one_launch):
     """The engine's gradient on the full batched workload (64 trajectories,
     9.07M samples) against the oracle on 64 random targets of every
-    trajectory.  alpha = beta = inf and a loose box make the projection the
+    trajectory, with the repulsion in its own kernel or as items of the one
+    engine launch.  alpha = beta = inf and a loose box make the projection the
     identity, so K' = K - eta G exposes G = (K - K') / eta; K in FP64 keeps
     that difference exact to ~1e-16 / eta."""
     probs = inputs.make_batched(seed=0)
@@ -181,7 +192,7 @@ def test_batched_workload_gradient(sp, ctx):
     gs = [sp.make_grid(r, p.grid.lo, p.grid.hi, p.grid.n) for r, p in zip(rhos, probs)]
     ps = [sp.make_proj(INF, INF, 10.0, 2) for _ in probs]
     etas = [p.eta for p in probs]
-    sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=False)
+    sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=False, one_launch=one_launch)
     sp.sparkling_status(ctx)
     out = K.cpu().numpy()
     rng = np.random.default_rng(8)

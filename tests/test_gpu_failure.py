@@ -34,7 +34,8 @@ def batch(seed=11, Ns=256, shots=(24, 9, 31)):
     return Ks, grids
 
 
-def test_wait_budget_timeout_is_reported_and_recoverable(sp):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_wait_budget_timeout_is_reported_and_recoverable(sp, one_launch):
     """With a zero wait budget, the batched step's projection items cannot
     wait for their trajectory's pair items (the last pair items are still
     running when the first projection item is dispensed): the step returns
@@ -54,7 +55,8 @@ def test_wait_budget_timeout_is_reported_and_recoverable(sp):
 
         def run():
             K = torch.from_numpy(K0).cuda()
-            sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=False)
+            sp.sparkling_step_batched(ctx, K, off, Ns, gs, etas, ps, graph=False,
+                                      one_launch=one_launch)
             return K
 
         ref = run()

@@ -8,8 +8,8 @@ against the FP64 oracle.
   sources paired), on 7,703 samples (8 target tiles, the last ragged) and a
   random density whose rows are not a multiple of 4: A, R, G and the energy,
   plain and regularised kernel;
-* the batched step (batched symmetric kernel + engine) with each repulsion
-  shape: the gradient recovered from an unconstrained step.
+* the two-launch batched step (batched symmetric kernel + engine) with each
+  repulsion shape: the gradient recovered from an unconstrained step.
 """
 import numpy as np
 import pytest
@@ -105,7 +105,7 @@ def test_batched_step_with_each_repulsion_shape(sp, variant):
         rhos = [torch.from_numpy(g.rho).cuda() for g in grids]
         gs = [sp.make_grid(r, g.lo, g.hi, g.n) for r, g in zip(rhos, grids)]
         ps = [sp.make_proj(INF, INF, 10.0, 3) for _ in grids]
-        sp.sparkling_step_batched(c, K, off, Ns, gs, etas, ps, graph=False)
+        sp.sparkling_step_batched(c, K, off, Ns, gs, etas, ps, graph=False, one_launch=False)
         sp.sparkling_status(c)
         out = K.cpu().numpy()
     finally:
