@@ -445,9 +445,15 @@ SPARKLING_API int sparkling_set_attraction(sparkling_ctx *ctx, int mode);
  *     needs them (blocking; about 384 M^3 bytes of temporary device memory,
  *     M = n_cells + 2g), again when the mesh or the regularisation changes;
  *     the context then keeps about 330 M^3 bytes (spectra, FFT and charge
- *     buffers) plus 80 bytes per sample.  A sample outside the mesh gives SPARKLING_E_RANGE.  Each
- *     evaluation reads the size of its short-range work list back to the
- *     host (one stream synchronisation), so it cannot be stream-captured.
+ *     buffers) plus 80 bytes per sample.  A sample outside the mesh gives
+ *     SPARKLING_E_RANGE.  The first evaluation of a sample count sizes the
+ *     buffers and waits once for the length of its short-range work list;
+ *     later evaluations of that count are asynchronous (the list's length is
+ *     read on the device), so after one such call outside any stream
+ *     capture they can be captured into a CUDA graph.  A captured call that
+ *     would have to size buffers returns SPARKLING_E_INVAL; a graph captured
+ *     before a call with another sample count (which resizes them) must be
+ *     captured again.
  * Returns SPARKLING_E_INVAL for a bad mode or mesh. */
 SPARKLING_API int sparkling_set_repulsion(sparkling_ctx *ctx, int mode, const sparkling_mesh *mesh);
 

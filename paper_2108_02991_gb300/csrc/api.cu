@@ -706,15 +706,16 @@ int run_pairs(sparkling_ctx *ctx, const void *K, int K_dtype, const sparkling_gr
         if ((s = ensure_mesh(ctx, st))) return s;
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(st, &cap));
-        if (cap != cudaStreamCaptureStatusNone)
-            return fail(ctx, SPARKLING_E_INVAL,
-                        "the mesh repulsion reads its work size back and cannot be captured");
         r_direct = at<dacc4>(ctx, P.o_rdir);
         const char *what = "";
         int nk = 0;
         LaunchScope ls(ctx, SPARKLING_KERNEL_REPULSION, st);
         cudaError_t e = mesh_eval(ctx->mesh, pos, P.N, energy, r_direct, ctx->d_status, ctx->sms, st,
-                                  &what, &nk);
+                                  &what, &nk, cap != cudaStreamCaptureStatusNone);
+        if (e == cudaErrorStreamCaptureUnsupported)
+            return fail(ctx, SPARKLING_E_INVAL,
+                        "the fast repulsion's buffers for N = %lld are allocated by a first call "
+                        "of that size outside stream capture", (long long)P.N);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
             return fail(ctx, SPARKLING_E_NOMEM, "fast repulsion: %s allocation failed", what);

@@ -225,8 +225,11 @@ int mesh_guard(int n_cells);
 bool mesh_matches(const MeshState *m, const MeshConfig &c);
 cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t st,
                        const char **what);
+// no_alloc: a call under stream capture; cudaErrorStreamCaptureUnsupported
+// where a buffer would have to grow.
 cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, dacc4 *out,
-                      int *status, int sms, cudaStream_t st, const char **what, int *launches);
+                      int *status, int sms, cudaStream_t st, const char **what, int *launches,
+                      bool no_alloc);
 
 // Multi-resolution driver (driver.cu).  dtype: 0 float, 1 double.
 cudaError_t launch_upsample(const void *Kc, void *Kf, int dtype, int64_t Nc, int64_t d, int sms,

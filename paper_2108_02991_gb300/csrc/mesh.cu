@@ -394,40 +394,60 @@ __global__ void count_items_kernel(const int *__restrict__ start, const int *__r
     }
 }
 
+// The short-range work list, numbered on the device: cell c owns items
+// [offsets[c], offsets[c] + counts[c]) (an exclusive scan of the counts),
+// ceil(n_c / kShortChunk) target chunks times slices[c] source slices of
+// its neighbour rows.  The kernels read its length on the device: the items
+// below the stored list's capacity are written by fill_items_kernel (one
+// thread per item) and read by the short-range kernel, which decodes any
+// item beyond the capacity itself.
 // Item u -> (targets t0, tn; sources s0, sn), all sorted positions.
-__global__ void fill_items_kernel(const int *__restrict__ offsets, const int *__restrict__ slices,
-                                  const int *__restrict__ start, const int *__restrict__ end,
-                                  int nc, int64_t total, int4 *items)
+__device__ int4 item_at(int64_t u, const int *__restrict__ offsets, const int *__restrict__ slices,
+                        const int *__restrict__ start, const int *__restrict__ end, int nc)
 {
     const int ncell = nc * nc * nc;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = ncell - 1;            // largest c with offsets[c] <= u
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int64_t)offsets[mid] <= u) lo = mid;
-            else hi = mid - 1;
-        }
-        const int c = lo;
-        const int local = (int)(u - offsets[c]), sl = slices[c];
-        const int k = local / sl;
-        int rs = local % sl;
-        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-        int4 it = make_int4(start[c] + k * kShortChunk, 0, 0, 0);
-        it.y = min(kShortChunk, end[c] - it.x);
-        for (int r = 0; r < kRows; ++r) {
-            int j0, j1;
-            if (!row_range(cx, cy, cz, r, nc, start, end, j0, j1)) continue;
-            const int ns = (j1 - j0 + kShortSlice - 1) / kShortSlice;
-            if (rs < ns) {
-                it.z = j0 + rs * kShortSlice;
-                it.w = min(kShortSlice, j1 - it.z);
-                break;
-            }
-            rs -= ns;
-        }
-        items[u] = it;
+    int lo = 0, hi = ncell - 1;                // largest c with offsets[c] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)offsets[mid] <= u) lo = mid;
+        else hi = mid - 1;
     }
+    const int c = lo;
+    const int local = (int)(u - offsets[c]), sl = slices[c];
+    int4 it = make_int4(0, 0, 0, 0);
+    if (sl <= 0 || local < 0) return it;
+    const int k = local / sl;
+    int rs = local % sl;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    it.x = start[c] + k * kShortChunk;
+    it.y = min(kShortChunk, end[c] - it.x);
+    for (int r = 0; r < kRows; ++r) {
+        int j0, j1;
+        if (!row_range(cx, cy, cz, r, nc, start, end, j0, j1)) continue;
+        const int ns = (j1 - j0 + kShortSlice - 1) / kShortSlice;
+        if (rs < ns) {
+            it.z = j0 + rs * kShortSlice;
+            it.w = min(kShortSlice, j1 - it.z);
+            break;
+        }
+        rs -= ns;
+    }
+    return it;
+}
+
+// The list's length, and its first `cap` items stored (grid-stride).
+__global__ void fill_items_kernel(const int *__restrict__ counts, const int *__restrict__ offsets,
+                                  const int *__restrict__ slices, const int *__restrict__ start,
+                                  const int *__restrict__ end, int nc, int64_t cap, int4 *items,
+                                  long long *total_out)
+{
+    const int ncell = nc * nc * nc;
+    const int64_t total = (int64_t)offsets[ncell - 1] + counts[ncell - 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *total_out = total;
+    const int64_t n = total < cap ? total : cap;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x)
+        items[u] = item_at(u, offsets, slices, start, end, nc);
 }
 
 // Short-range pair term of target p and source q, added to f (force) or
@@ -456,51 +476,78 @@ __device__ __forceinline__ void short_pair(const float4 p, const float4 q, float
     }
 }
 
+// One item: targets [it.x, it.x + it.y) (two per lane) against sources
+// [it.z, it.z + it.w) of the sorted positions, the sums added to the targets'
+// fixed-point accumulators.
+template <bool ENERGY>
+__device__ __forceinline__ void short_item(const int4 it, int lane, const float4 *__restrict__ spos,
+                                           const int *__restrict__ idx, float rc2, float inv_sigma,
+                                           float spi, float eps2, unsigned long long *acc)
+{
+    constexpr int NV = ENERGY ? 1 : 3;
+    float4 p[2];
+    bool ok[2];
+    float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (int t = 0; t < 2; ++t) {
+        const int l = lane + 32 * t;
+        ok[t] = l < it.y;
+        p[t] = ok[t] ? spos[it.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 *src = spos + it.z;
+#pragma unroll 4
+    for (int j = 0; j < it.w; ++j) {
+        const float4 q = __ldg(src + j);
+        short_pair<ENERGY>(p[0], q, rc2, inv_sigma, spi, eps2, f[0]);
+        short_pair<ENERGY>(p[1], q, rc2, inv_sigma, spi, eps2, f[1]);
+    }
+    for (int t = 0; t < 2; ++t) {
+        if (!ok[t]) continue;
+        unsigned long long *a = acc + (int64_t)idx[it.x + lane + 32 * t] * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const long long x = __float2ll_rn(f[t][v] * 4294967296.0f);
+            if (x) atomicAdd(a + v, (unsigned long long)x);
+        }
+    }
+}
+
 // Persistent warps take items from a queue: kShortChunk targets of one cell
 // (two per lane) against up to kShortSlice sources of one neighbour row.
 // The lanes of a warp read the same source at the same time (one broadcast
 // load serves 64 pairs); the item sums are added to the targets' 64-bit
 // fixed-point accumulators (exact, order-free).  Small items keep the lanes
-// busy where cells hold few samples.
+// busy where cells hold few samples.  The length of the list is read on the
+// device; items below `cap` come from the stored list, the rest are decoded
+// here: nothing about the work list goes through the host, so an evaluation
+// can be captured in a CUDA graph.
 template <bool ENERGY>
 __global__ void __launch_bounds__(kShortThreads) short_items_kernel(
-    const int4 *__restrict__ items, const int *__restrict__ n_items, unsigned int *queue,
-    const float4 *__restrict__ spos, const int *__restrict__ idx, float rc2, float inv_sigma,
-    float spi, float eps2, unsigned long long *acc)
+    const int4 *__restrict__ items, int64_t cap, const int *__restrict__ counts,
+    const int *__restrict__ offsets, const int *__restrict__ slices, const int *__restrict__ start,
+    const int *__restrict__ end, int nc, unsigned int *queue, const float4 *__restrict__ spos,
+    const int *__restrict__ idx, float rc2, float inv_sigma, float spi, float eps2,
+    unsigned long long *acc)
 {
-    constexpr int NV = ENERGY ? 1 : 3;
     const int lane = threadIdx.x & 31;
-    const int total = *n_items;
+    const int ncell = nc * nc * nc;
+    const int64_t total = (int64_t)offsets[ncell - 1] + counts[ncell - 1];
     for (;;) {
-        int u = 0;
-        if (lane == 0) u = (int)atomicAdd(queue, 1u);
+        int64_t u = 0;
+        if (lane == 0) u = atomicAdd(queue, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= total) break;
-        const int4 it = items[u];
-        float4 p[2];
-        bool ok[2];
-        float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        for (int t = 0; t < 2; ++t) {
-            const int l = lane + 32 * t;
-            ok[t] = l < it.y;
-            p[t] = ok[t] ? spos[it.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 it;
+        if (u < cap) {
+            it = items[u];
+        } else {                               // beyond the stored list: decode it here
+            if (lane == 0) it = item_at(u, offsets, slices, start, end, nc);
+            it.x = __shfl_sync(0xffffffffu, it.x, 0);
+            it.y = __shfl_sync(0xffffffffu, it.y, 0);
+            it.z = __shfl_sync(0xffffffffu, it.z, 0);
+            it.w = __shfl_sync(0xffffffffu, it.w, 0);
         }
-        const float4 *src = spos + it.z;
-#pragma unroll 4
-        for (int j = 0; j < it.w; ++j) {
-            const float4 q = __ldg(src + j);
-            short_pair<ENERGY>(p[0], q, rc2, inv_sigma, spi, eps2, f[0]);
-            short_pair<ENERGY>(p[1], q, rc2, inv_sigma, spi, eps2, f[1]);
-        }
-        for (int t = 0; t < 2; ++t) {
-            if (!ok[t]) continue;
-            unsigned long long *a = acc + (int64_t)idx[it.x + lane + 32 * t] * NV;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const long long x = __float2ll_rn(f[t][v] * 4294967296.0f);
-                if (x) atomicAdd(a + v, (unsigned long long)x);
-            }
-        }
+        if (it.y > 0 && it.w > 0)
+            short_item<ENERGY>(it, lane, spos, idx, rc2, inv_sigma, spi, eps2, acc);
     }
 }
 
@@ -550,10 +597,10 @@ struct MeshState {
     float4 *spos = nullptr; size_t spos_cap = 0;
     unsigned long long *shortr = nullptr; size_t shortr_cap = 0;   // fixed point [N][3]
     int *cellwork = nullptr; size_t cellwork_cap = 0;   // counts, slices, offsets [ncell] each
-    int4 *items = nullptr; size_t items_cap = 0;
-    int *small = nullptr;                               // n_items, queue
+    int4 *items = nullptr; size_t items_cap = 0;        // the stored part of the work list
+    int64_t items_n = -1;                               // the sample count it was sized for
+    unsigned long long *dsmall = nullptr;               // [0]: item queue, [1]: list length
     int short_ctas[2] = {0, 0};                         // persistent CTAs (gradient, energy)
-    int host_small[2] = {0, 0};                         // source of the n_items / queue upload
     void *cub = nullptr; size_t cub_cap = 0;
 };
 
@@ -566,7 +613,7 @@ void mesh_state_destroy(MeshState *m)
     cudaFree(m->spectra); cudaFree(m->Q); cudaFree(m->box); cudaFree(m->qhat); cudaFree(m->tmp);
     cudaFree(m->keys); cudaFree(m->vals); cudaFree(m->ranges); cudaFree(m->spos);
     cudaFree(m->shortr); cudaFree(m->cub); cudaFree(m->cellwork); cudaFree(m->items);
-    cudaFree(m->small);
+    cudaFree(m->dsmall);
     delete m;
 }
 
@@ -726,9 +773,15 @@ cudaError_t mesh_build(MeshState *m, const MeshConfig &c, int sms, cudaStream_t 
 
 // Repulsion sums of the N packed samples into out[i] = (sum d/r, sum |d|_eps)
 // over all j (directed, the self pair included as eps in the potential).
-// Reads the number of short-range work items back to the host (one sync).
+// Asynchronous: once the buffers have their size for N (the first call of a
+// sample count allocates them and waits once for the length of its
+// short-range work list), a call only enqueues work on `st` and can be
+// captured.
+// no_alloc (a call under stream capture): return cudaErrorStreamCaptureUnsupported
+// instead of growing a buffer.
 cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, dacc4 *out,
-                      int *status, int sms, cudaStream_t st, const char **what, int *launches)
+                      int *status, int sms, cudaStream_t st, const char **what, int *launches,
+                      bool no_alloc)
 {
     const MeshConfig &c = m->cfg;
     const int M = m->M, L = m->L, nc = m->nc;
@@ -746,6 +799,19 @@ cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, d
                                     (int)N, 0, end_bit, st);
     cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, m->cellwork, m->cellwork, ncell, st);
     const size_t cub_bytes = std::max(sort_bytes, scan_bytes);
+    if (no_alloc &&
+        (nm * sizeof(unsigned long long) > m->Q_cap ||
+         (size_t)(nfield + 1) * nl * sizeof(float) > m->box_cap ||
+         nlc * sizeof(cufftComplex) > m->qhat_cap || nlc * sizeof(cufftComplex) > m->tmp_cap ||
+         (size_t)2 * N * sizeof(unsigned int) > m->keys_cap ||
+         (size_t)2 * N * sizeof(int) > m->vals_cap ||
+         (size_t)2 * ncell * sizeof(int) > m->ranges_cap ||
+         (size_t)N * sizeof(float4) > m->spos_cap ||
+         (size_t)N * 3 * sizeof(unsigned long long) > m->shortr_cap ||
+         (size_t)3 * ncell * sizeof(int) > m->cellwork_cap || cub_bytes + 256 > m->cub_cap ||
+         !m->dsmall || !m->short_ctas[0] || m->items_n != N))
+        return cudaErrorStreamCaptureUnsupported;
+
     if ((err = grow(m->Q, m->Q_cap, nm * sizeof(unsigned long long))) ||
         (err = grow(m->box, m->box_cap, (size_t)(nfield + 1) * nl * sizeof(float))) ||
         (err = grow(m->qhat, m->qhat_cap, nlc * sizeof(cufftComplex))) ||
@@ -758,7 +824,7 @@ cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, d
         (err = grow(m->cellwork, m->cellwork_cap, (size_t)3 * ncell * sizeof(int))) ||
         (err = grow(m->cub, m->cub_cap, cub_bytes + 256)))
         return err;
-    if (!m->small && (err = cudaMalloc(&m->small, 4 * sizeof(int)))) return err;
+    if (!m->dsmall && (err = cudaMalloc(&m->dsmall, 2 * sizeof(unsigned long long)))) return err;
     if (!m->short_ctas[0]) {
         int a = 0, b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, short_items_kernel<false>, kShortThreads, 0);
@@ -786,34 +852,48 @@ cudaError_t mesh_eval(MeshState *m, const float4 *pos, int64_t N, bool energy, d
     count_items_kernel<<<gC, kMeshThreads, 0, st>>>(start, end, nc, counts, slices);
     if ((err = cub::DeviceScan::ExclusiveSum(m->cub, scan_bytes, counts, offsets, ncell, st)))
         return err;
-    int h2[2];
-    if ((err = cudaMemcpyAsync(&h2[0], offsets + ncell - 1, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
-        (err = cudaMemcpyAsync(&h2[1], counts + ncell - 1, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
-        (err = cudaStreamSynchronize(st)))
-        return err;
-    const int64_t total = (int64_t)h2[0] + h2[1];
-    if (total > ((int64_t)1 << 31) - 1) return cudaErrorInvalidValue;
-    if ((err = grow(m->items, m->items_cap, (size_t)std::max<int64_t>(total, 1) * sizeof(int4))))
-        return err;
-    m->host_small[0] = (int)total;
-    m->host_small[1] = 0;
-    if ((err = cudaMemcpyAsync(m->small, m->host_small, 2 * sizeof(int), cudaMemcpyHostToDevice, st)))
-        return err;
-    if (total > 0)
-        fill_items_kernel<<<grid_for(total, sms), kMeshThreads, 0, st>>>(offsets, slices, start,
-                                                                         end, nc, total, m->items);
+    unsigned int *queue = reinterpret_cast<unsigned int *>(m->dsmall);
+    long long *d_total = reinterpret_cast<long long *>(m->dsmall + 1);
+    if (!no_alloc && m->items_n != N) {
+        // The first evaluation of a sample count sizes the stored list: it
+        // waits once for the list's length and keeps room for half as many
+        // again (the list changes as the samples move; any items beyond the
+        // room are decoded by the short-range kernel).  The list is not
+        // reallocated while the sample count stays the same.
+        fill_items_kernel<<<1, 32, 0, st>>>(counts, offsets, slices, start, end, nc, 0, nullptr,
+                                            d_total);
+        ++nk;
+        long long total = 0;
+        if ((err = cudaMemcpyAsync(&total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, st)) ||
+            (err = cudaStreamSynchronize(st)))
+            return err;
+        const size_t want = (size_t)std::max<long long>(total, 0);
+        const size_t bytes = (want + want / 2 + 1024) * sizeof(int4);
+        cudaFree(m->items);
+        m->items = nullptr;
+        m->items_cap = 0;
+        m->items_n = -1;
+        if ((err = cudaMalloc(&m->items, bytes))) return err;
+        m->items_cap = bytes;
+        m->items_n = N;
+    }
+    const int64_t cap = (int64_t)(m->items_cap / sizeof(int4));
+    if ((err = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st))) return err;
+    fill_items_kernel<<<grid_for(std::max<int64_t>(cap, 1), sms), kMeshThreads, 0, st>>>(
+        counts, offsets, slices, start, end, nc, cap, m->items, d_total);
     if ((err = cudaMemsetAsync(m->shortr, 0, (size_t)N * NV * sizeof(unsigned long long), st)))
         return err;
     const float rc2 = (float)(c.rc * c.rc), inv_sigma = (float)(1.0 / c.sigma);
     const float spi = (float)(c.sigma * 0.56418958354775628);
     const float eps2 = (float)(c.eps * c.eps);
-    unsigned int *queue = reinterpret_cast<unsigned int *>(m->small + 1);
     if (energy)
         short_items_kernel<true><<<m->short_ctas[1], kShortThreads, 0, st>>>(
-            m->items, m->small, queue, m->spos, m->vals + N, rc2, inv_sigma, spi, eps2, m->shortr);
+            m->items, cap, counts, offsets, slices, start, end, nc, queue, m->spos, m->vals + N,
+            rc2, inv_sigma, spi, eps2, m->shortr);
     else
         short_items_kernel<false><<<m->short_ctas[0], kShortThreads, 0, st>>>(
-            m->items, m->small, queue, m->spos, m->vals + N, rc2, inv_sigma, spi, eps2, m->shortr);
+            m->items, cap, counts, offsets, slices, start, end, nc, queue, m->spos, m->vals + N,
+            rc2, inv_sigma, spi, eps2, m->shortr);
     nk += 6;
     // long-range part
     if ((err = cudaMemsetAsync(m->Q, 0, nm * sizeof(unsigned long long), st))) return err;

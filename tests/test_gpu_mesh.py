@@ -8,7 +8,9 @@ particle-mesh summation through the C ABI.
 * the NumPy restatement of the library's mesh (tests/mesh_reference.py) is
   printed beside the result as a diagnostic only -- it follows the library's
   own design, so agreement with it proves nothing and no gate rests on it;
-* a sample outside the mesh is reported, repeated calls are bitwise equal.
+* a sample outside the mesh is reported, repeated calls are bitwise equal;
+* an evaluation captured in a CUDA graph (after one call of the same size
+  outside capture) replays bit for bit the eager result.
 """
 import math
 
@@ -131,6 +133,53 @@ def test_mesh_repeatable_and_range_error(sp):
         assert e.value.code == sp.E_RANGE
         G3, _, _ = gpu_grad(sp, ctx, K, grid)          # the context stays usable
         np.testing.assert_array_equal(G3, G1)
+    finally:
+        ctx.close()
+
+
+def test_mesh_evaluation_captured_in_a_cuda_graph(sp):
+    """The mesh path sizes and reads its short-range work list on the device,
+    so a gradient call can be captured: one eager call sizes the buffers,
+    then the same call captured into a CUDA graph and replayed twice (after
+    K changed in place and back) gives the eager G bit for bit, and the
+    replay with the changed K matches an eager call on it."""
+    rng = np.random.default_rng(63)
+    K = rng.uniform(-0.45, 0.45, size=(6000, 3)).astype(np.float32)
+    K2 = np.clip(K + rng.normal(scale=2e-3, size=K.shape), -0.45, 0.45).astype(np.float32)
+    grid = inputs.density_gaussian(8, 0.2)
+    ctx = mesh_ctx(sp, 24)
+    try:
+        Kd = torch.from_numpy(K).cuda()
+        rho = torch.from_numpy(grid.rho).cuda()
+        g = sp.make_grid(rho, grid.lo, grid.hi, grid.n)
+        G = torch.empty(K.shape[0], 3, dtype=torch.float64, device="cuda")
+        sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G)
+        sp.sparkling_status(ctx)
+        eager = G.cpu().numpy()
+        Kd.copy_(torch.from_numpy(K2))
+        sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G)
+        sp.sparkling_status(ctx)
+        eager2 = G.cpu().numpy()
+        Kd.copy_(torch.from_numpy(K))
+        G.zero_()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+            sp.sparkling_grad(ctx, Kd, g, sp.ACC_KAHAN32, G=G)
+        graph.replay()
+        torch.cuda.synchronize()
+        sp.sparkling_status(ctx)
+        np.testing.assert_array_equal(G.cpu().numpy(), eager)
+        Kd.copy_(torch.from_numpy(K2))
+        graph.replay()
+        torch.cuda.synchronize()
+        sp.sparkling_status(ctx)
+        np.testing.assert_array_equal(G.cpu().numpy(), eager2)
+        Kd.copy_(torch.from_numpy(K))
+        graph.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(G.cpu().numpy(), eager)
+        assert not np.array_equal(eager, eager2)
     finally:
         ctx.close()
 
