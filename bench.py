@@ -65,6 +65,9 @@ def parse_args(argv=None):
     ap.add_argument("--acc", choices=("kahan", "fp64", "fp64pair"), default="kahan",
                     help="per-target accumulation: compensated FP32 folds, FP64 folds, or the "
                          "plain FP64-accumulate form (every attraction pair term added in FP64)")
+    ap.add_argument("--trajectories", type=int, default=64,
+                    help="batched workload: keep the first B of its 64 trajectories (a smaller "
+                         "launch of the same kernels, e.g. for a profiler capture)")
     ap.add_argument("--two-launches", action="store_true",
                     help="batched step: the symmetric repulsion in its own kernel ahead of the "
                          "engine instead of as items of the engine's work list (one launch)")
@@ -374,7 +377,7 @@ class Workload:
                     "fp64pair": sp.ACC_FP64_PAIR}[args.acc]
         if args.workload == "batched":
             import inputs
-            self.probs = inputs.make_batched(seed=seed)
+            self.probs = inputs.make_batched(seed=seed)[:max(1, args.trajectories)]
         else:
             self.probs = [load_problem(args.workload, seed, args.shot_stride)]
         self.batched = args.workload == "batched" or args.path == "engine"
@@ -389,6 +392,7 @@ class Workload:
         self.Kh = torch.from_numpy(K).pin_memory()
         self.rhoh = [torch.from_numpy(p.grid.rho).pin_memory() for p in self.probs]
         self.K = self.Kh.to(dev)
+        self.host_current = True        # Kh holds the latest pattern (else K on the device)
         self.rhos = [r.to(dev) for r in self.rhoh]
         self.grids = [sp.make_grid(r, p.grid.lo, p.grid.hi, p.grid.n)
                       for r, p in zip(self.rhos, self.probs)]
@@ -408,8 +412,32 @@ class Workload:
         self.kbytes = int(self.Kh.numel() * self.Kh.element_size())
         self.rhobytes = int(sum(r.numel() * r.element_size() for r in self.rhoh))
 
+    def constraint_excess(self):
+        """Largest constraint excess of the current pattern over all shots
+        (eq. constraints): max |k[n+1]-k[n]| / alpha - 1, max
+        |k[n+2]-2k[n+1]+k[n]| / beta - 1 and max |k|_inf - box; <= 0 where
+        the pattern is feasible.  The steps run a fixed number of projection
+        iterations, so small positive excesses are expected."""
+        import numpy as np
+        K = (self.Kh if self.host_current else self.K.cpu()).numpy().astype(np.float64)
+        ea = eb = ex = -np.inf
+        for b, p in enumerate(self.probs):
+            S = K[self.off[b]:self.off[b + 1]].reshape(p.Nc, p.Ns, 3)
+            if p.Ns > 1 and np.isfinite(p.proj.alpha):
+                d1 = np.sqrt(((S[:, 1:] - S[:, :-1]) ** 2).sum(-1)).max()
+                ea = max(ea, d1 / p.proj.alpha - 1.0)
+            if p.Ns > 2 and np.isfinite(p.proj.beta):
+                d2 = np.sqrt(((S[:, 2:] - 2.0 * S[:, 1:-1] + S[:, :-2]) ** 2).sum(-1)).max()
+                eb = max(eb, d2 / p.proj.beta - 1.0)
+            ex = max(ex, float(np.abs(S).max()) - p.proj.box)
+        return {"alpha_rel": float(ea), "beta_rel": float(eb), "box": float(ex),
+                "n_pit": int(self.probs[0].proj.n_iter),
+                "note": "largest excess over all shots of the pattern after the timed steps "
+                        "(<= 0: feasible); fixed-iteration projections"}
+
     def step_device(self):
         """One step on device-resident K (asynchronous)."""
+        self.host_current = False
         sp = self.sp
         if self.batched:
             sp.sparkling_step_batched(self.ctx, self.K, self.off, self.Ns, self.grids, self.etas,
@@ -426,6 +454,7 @@ class Workload:
         (the batched step), else None (the library's STEP scope times it)."""
         import torch
         sp = self.sp
+        self.host_current = True
         if not self.batched:
             p = self.probs[0]
             sp.sparkling_step_host(self.ctx, self.Kh, p.Nc, p.Ns, self.hgrid, self.rhoh[0],
@@ -586,8 +615,11 @@ def run_ours(args):
     rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
     peak = sms * rate * max_mhz * 1e6
     if w.batched:
-        # one engine launch runs every pair of the step: N_b*P_b + N_b*(N_b-1)
-        kname, kpairs = "engine", w.pairs
+        # the engine (with the symmetric repulsion, as its items or in the
+        # kernel ahead of it) takes one reciprocal square root per attraction
+        # pair and one per unordered repulsion pair: N_b*P_b + N_b*(N_b-1)/2
+        kname = "engine"
+        kpairs = sum(p.N * int(p.grid.rho.size) + p.N * (p.N - 1) // 2 for p in w.probs)
     elif args.attraction == "field" and args.repulsion == "direct":
         # the attraction is an interpolation; the symmetric repulsion takes
         # one reciprocal square root per unordered pair
@@ -610,6 +642,10 @@ def run_ours(args):
             "peak_basis": f"{sms} SMs x {rate:g} MUFU.RSQ/clk/SM x {max_mhz:.0f} MHz max SM clock "
                           f"(one reciprocal square root per pair; probe measured "
                           f"{rsq if rsq else 'n/a'} RSQ/clk/SM)"}
+    if kname == "engine":
+        roof["unit"] = "G reciprocal square roots/s"
+        roof["note"] = ("achieved counts the step's reciprocal square roots: one per attraction "
+                        "pair and one per unordered repulsion pair (N_b*P_b + N_b*(N_b-1)/2)")
     if traffic:
         roof["traffic_basis"] = traffic["basis"]
     if clk and achieved:
@@ -659,6 +695,7 @@ def run_ours(args):
                                   f"repulsion {args.shape_repulsion} (-1: autotuned)")},
             "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
+            "constraints": w.constraint_excess(),
             "seconds_per_iteration": total_ms / args.steps / 1e3,
             "step_ms": [round(v, 3) for v in step_ms],
             "autotuner": [l for l in sp.sparkling_tuning_report(ctx).splitlines() if l],
