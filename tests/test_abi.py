@@ -45,6 +45,24 @@ def test_exports_every_declared_symbol(lib):
 
 
 @needs_nvcc
+def test_binding_constants_match_the_header(lib):
+    """Every integer #define of sparkling.h that the binding also names
+    (without the SPARKLING_ prefix) has the same value there; the kernel
+    kinds are the binding's KERNEL_NAMES in header order."""
+    sp = lib
+    text = open(HEADER).read()
+    consts = dict((n, int(v)) for n, v in re.findall(r"#define SPARKLING_(\w+)\s+(-?\d+)", text))
+    shared = [n for n in consts if hasattr(sp, n)]
+    assert len(shared) >= 20
+    for n in shared:
+        assert getattr(sp, n) == consts[n], f"SPARKLING_{n}"
+    kinds = sorted((v, n) for n, v in consts.items()
+                   if n.startswith("KERNEL_") and n != "KERNEL_COUNT")
+    assert [n[len("KERNEL_"):].lower() for _, n in kinds] == list(sp.KERNEL_NAMES)
+    assert consts["KERNEL_COUNT"] == len(sp.KERNEL_NAMES)
+
+
+@needs_nvcc
 def test_struct_layout_matches_c(lib, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
