@@ -59,9 +59,10 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("hr", "diff", "medium", "small", "tiny", "batched"),
                     default="hr")
-    ap.add_argument("--path", choices=("kernels", "engine"), default="kernels",
-                    help="single-trajectory step through sparkling_step (separate pair kernels) "
-                         "or the persistent engine (sparkling_step_batched with B = 1)")
+    ap.add_argument("--path", choices=("auto", "kernels", "engine"), default="auto",
+                    help="device path of the single-trajectory step (sparkling_set_step_path): "
+                         "the library's choice (the persistent engine from 2^22 samples on), the "
+                         "separate kernels, or the one-launch persistent engine")
     ap.add_argument("--acc", choices=("kahan", "fp64", "fp64pair"), default="kahan",
                     help="per-target accumulation: compensated FP32 folds, FP64 folds, or the "
                          "plain FP64-accumulate form (every attraction pair term added in FP64)")
@@ -111,8 +112,7 @@ def parse_args(argv=None):
         a.steps = 1 if a.workload == "hr" else 3
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if (a.attraction == "field" or a.repulsion == "mesh") and (a.workload == "batched"
-                                                               or a.path == "engine"):
+    if (a.attraction == "field" or a.repulsion == "mesh") and a.workload == "batched":
         ap.error("--attraction field / --repulsion mesh run on the kernels path "
                  "(the engine takes the direct sums)")
     return a
@@ -380,7 +380,7 @@ class Workload:
             self.probs = inputs.make_batched(seed=seed)[:max(1, args.trajectories)]
         else:
             self.probs = [load_problem(args.workload, seed, args.shot_stride)]
-        self.batched = args.workload == "batched" or args.path == "engine"
+        self.batched = args.workload == "batched"
         self.one_launch = not args.two_launches
         self.off = [0]
         for p in self.probs:
@@ -494,6 +494,7 @@ def run_ours(args):
         sp.sparkling_set_shape(ctx, "attraction", args.shape_attraction)
     if args.shape_repulsion >= 0:
         sp.sparkling_set_shape(ctx, "repulsion", args.shape_repulsion)
+    sp.sparkling_set_step_path(ctx, args.path)
     sp.sparkling_set_projection(ctx, sp.PROJECTION_MIXED if args.projection == "mixed"
                                 else sp.PROJECTION_FP64)
     stream = torch.cuda.current_stream(dev)
@@ -614,7 +615,7 @@ def run_ours(args):
     rsq = probe.get("rsqrt") if probe else None
     rate = float(round(rsq)) if rsq else float(SFU_RSQ_PER_SM_CLK)
     peak = sms * rate * max_mhz * 1e6
-    if w.batched:
+    if w.batched or ktimes["engine"][1]:
         # the engine (with the symmetric repulsion, as its items or in the
         # kernel ahead of it) takes one reciprocal square root per attraction
         # pair and one per unordered repulsion pair: N_b*P_b + N_b*(N_b-1)/2
@@ -684,8 +685,9 @@ def run_ours(args):
             "config": {"workload": w.desc, "N": w.N, "P": int(p0.grid.rho.size),
                        "trajectories": len(w.probs), "Ns": w.Ns, "pairs_per_step": w.pairs,
                        "n_pit": p0.proj.n_iter,
-                       "path": ("engine, one launch" if w.one_launch else "engine")
-                       if w.batched else "kernels",
+                       "path": (("engine, one launch" if w.one_launch else "engine")
+                                if w.batched else
+                                "engine, one launch" if ktimes["engine"][1] else "kernels"),
                        "l2": "flushed (512 MB write) before every step", "acc": args.acc,
                        "projection": args.projection,
                        "attraction": args.attraction, "repulsion": args.repulsion,

@@ -136,6 +136,11 @@ typedef struct sparkling_proj {
 #define SPARKLING_PROJECTION_FP64 0    /* duals, primal and step in FP64 for every K dtype (default) */
 #define SPARKLING_PROJECTION_MIXED 1   /* FP32 K, fixed n_iter: FP32 iteration on s - k and the duals */
 
+/* How sparkling_step runs its device work (sparkling_set_step_path). */
+#define SPARKLING_STEP_AUTO 0      /* the persistent engine from 2^22 samples on, else the kernels (default) */
+#define SPARKLING_STEP_KERNELS 1   /* attraction, repulsion, combine and projection kernels in turn */
+#define SPARKLING_STEP_ENGINE 2    /* the one-launch persistent engine wherever it applies */
+
 /* How the attraction term is evaluated (sparkling_set_attraction). */
 #define SPARKLING_ATTRACTION_DIRECT 0   /* direct sum over the grid: O(N P) */
 #define SPARKLING_ATTRACTION_FIELD 1    /* interpolated node field: O(N), approximate */
@@ -239,8 +244,13 @@ SPARKLING_API int sparkling_project(sparkling_ctx *ctx, void *K, int K_dtype, in
  * the workspace; the step and the projection run in FP64 (unless the
  * context chose SPARKLING_PROJECTION_MIXED) and the result is rounded to
  * K_dtype.  With timing on, the device work of the call is also timed as one
- * SPARKLING_KERNEL_STEP scope.  Asynchronous unless converged mode is
- * requested. */
+ * SPARKLING_KERNEL_STEP scope.  The device work runs either as the separate
+ * kernels or as one launch of the persistent engine (sparkling_step_batched
+ * with B = 1: the same arithmetic, attraction and symmetric repulsion items
+ * sharing the SMs), as sparkling_set_step_path chooses; the engine applies
+ * with direct sums, ACC_KAHAN32 or ACC_FP64 and a fixed n_iter.
+ * Asynchronous on the kernels path unless converged mode is requested; the
+ * engine path first waits for the stream's earlier work. */
 SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64_t Nc, int64_t Ns,
                                  const sparkling_grid *grid, int acc, double eta,
                                  const sparkling_proj *proj, void *stream);
@@ -391,6 +401,17 @@ SPARKLING_API int sparkling_set_regularisation(sparkling_ctx *ctx, double eps);
  *     k + e in FP64); FP64 K and converged mode keep the FP64 iteration.
  * Returns SPARKLING_E_INVAL for another mode. */
 SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode);
+
+/* Device path of the context's sparkling_step and sparkling_step_host calls
+ * (SPARKLING_STEP_*).  AUTO (default) takes the one-launch persistent engine
+ * for steps of 2^22 samples or more (on the 1e7-sample workload it is ~8 %
+ * faster than the kernels in turn, since SFU-bound attraction items and
+ * FP32-bound repulsion items share each SM) and the kernels below that;
+ * ENGINE takes the engine at every size; KERNELS never.  Steps the engine
+ * does not cover (fast summation modes, ACC_FP64_PAIR, converged mode) run
+ * on the kernels whatever the setting.  Returns SPARKLING_E_INVAL for
+ * another value. */
+SPARKLING_API int sparkling_set_step_path(sparkling_ctx *ctx, int path);
 
 /* Budget of the context's bounded device waits (a TMA copy's mbarrier, the
  * batched step's wait for a trajectory's pair items), in SM clock cycles;

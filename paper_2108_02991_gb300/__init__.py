@@ -22,6 +22,8 @@ KERNEL_NAMES = ("pack", "attraction", "repulsion", "combine", "project", "engine
 PROJECTION_FP64, PROJECTION_MIXED = 0, 1
 BATCH_GRAPH = 1
 BATCH_TWO_LAUNCHES = 2
+STEP_AUTO, STEP_KERNELS, STEP_ENGINE = 0, 1, 2
+STEP_PATHS = ("auto", "kernels", "engine")
 ATTRACTION_DIRECT, ATTRACTION_FIELD = 0, 1
 REPULSION_DIRECT, REPULSION_MESH = 0, 1
 
@@ -35,7 +37,7 @@ ABI_SYMBOLS = (
     "sparkling_set_attraction", "sparkling_attraction_field", "sparkling_set_regularisation",
     "sparkling_upsample", "sparkling_optimize", "sparkling_multires", "sparkling_set_repulsion",
     "sparkling_set_shape", "sparkling_set_projection", "sparkling_set_wait_budget",
-    "sparkling_set_memory_limit",
+    "sparkling_set_memory_limit", "sparkling_set_step_path",
 )
 
 
@@ -128,6 +130,7 @@ def lib() -> ctypes.CDLL:
             "sparkling_attraction_field": ([p, p, p], i),
             "sparkling_set_regularisation": ([p, ctypes.c_double], i),
             "sparkling_set_projection": ([p, i], i),
+            "sparkling_set_step_path": ([p, i], i),
             "sparkling_set_wait_budget": ([p, i64], i),
             "sparkling_set_memory_limit": ([p, i64], i),
             "sparkling_set_repulsion": ([p, i, p], i),
@@ -406,6 +409,12 @@ def sparkling_set_projection(ctx: Context, mode: int) -> None:
     """PROJECTION_FP64 (default: FP64 iteration for every K dtype) or
     PROJECTION_MIXED (FP32 K: FP32 iteration on the displacement)."""
     _check(ctx, lib().sparkling_set_projection(ctx.handle, int(mode)))
+
+
+def sparkling_set_step_path(ctx: Context, path: str) -> None:
+    """Device path of sparkling_step / sparkling_step_host: "auto" (the
+    persistent engine from 2^22 samples on), "kernels" or "engine"."""
+    _check(ctx, lib().sparkling_set_step_path(ctx.handle, STEP_PATHS.index(path)))
 
 
 def sparkling_set_wait_budget(ctx: Context, cycles: int) -> None:

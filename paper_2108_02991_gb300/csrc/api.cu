@@ -23,6 +23,10 @@
 
 using namespace sparkling;
 
+// SPARKLING_STEP_AUTO: steps of this many samples or more take the
+// persistent engine (measured faster on the 1e7-sample workload).
+constexpr int64_t kStepEngineMin = (int64_t)1 << 22;
+
 struct sparkling_ctx {
     int device = 0;
     bool inited = false;
@@ -31,6 +35,7 @@ struct sparkling_ctx {
     long long wait_cycles = kWaitCycles;   // budget of the kernels' bounded waits
     size_t mem_limit = 0;       // cap on the context's device allocations (0: none)
     int proj_mode = SPARKLING_PROJECTION_FP64;
+    int step_path = SPARKLING_STEP_AUTO;
     double *d_small = nullptr;  // [0..1] energy, [2..5] violation bits, [6] notconv (int)
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -77,6 +82,8 @@ struct sparkling_ctx {
         size_t o_pos = 0, o_traj = 0, o_items = 0, o_cnt = 0, o_part = 0, o_gstate = 0, end = 0;
         bool sym = false;                 // repulsion by the batched symmetric kernel
         bool one_launch = false;          // symmetric repulsion items in the engine's work list
+        bool roles = false;               // role dispatch over the list's three parts
+        int32_t n_attr = 0, n_sym = 0;    // sizes of its attraction and symmetric parts
         size_t o_racc = 0, o_symtraj = 0;
         int64_t sym_units = 0;
         std::vector<SymTraj> symtraj;
@@ -1002,6 +1009,31 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
     while (released < B) project_items(released++);
 }
 
+// Role dispatch: the list reordered into its attraction items, its
+// symmetric items and its projection items, each part in list order.
+void split_work_list(sparkling_ctx::Batch &b)
+{
+    std::vector<EngineItem> items;
+    std::vector<double> pairs;
+    items.reserve(b.items.size());
+    pairs.reserve(b.items.size());
+    int32_t part[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        const int kind = k == 0 ? kItemAttraction : k == 1 ? kItemSym : kItemProject;
+        for (size_t i = 0; i < b.items.size(); ++i)
+            if (b.items[i].kind == kind) {
+                items.push_back(b.items[i]);
+                pairs.push_back(b.item_pairs[i]);
+                ++part[k];
+            }
+    }
+    b.items.swap(items);
+    b.item_pairs.swap(pairs);
+    b.n_attr = part[0];
+    b.n_sym = part[1];
+    b.n_lead_items = part[0] + part[1];
+}
+
 int validate_batch(sparkling_ctx *ctx, int32_t B, const int64_t *off, const void *K, int K_dtype,
                    int32_t Ns, const sparkling_grid *grids, const double *eta,
                    const sparkling_proj *proj, int acc)
@@ -1052,8 +1084,8 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
                  cudaStream_t st)
 {
     sparkling_ctx::Batch &b = ctx->batch;
-    CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0, (size_t)(b.B + 1) * sizeof(unsigned int),
-                       st));
+    CK(cudaMemsetAsync(at<unsigned int>(ctx, b.o_cnt), 0,
+                       (size_t)(3 + b.B + kSmSlots) * sizeof(unsigned int), st));
     EngineArgs e{};
     e.traj = at<EngineTraj>(ctx, b.o_traj);
     e.items = at<EngineItem>(ctx, b.o_items);
@@ -1064,7 +1096,11 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.K = K;
     e.part = at<dacc4>(ctx, b.o_part);
     e.queue = at<unsigned int>(ctx, b.o_cnt);
-    e.done = e.queue + 1;
+    e.done = e.queue + 3;
+    e.sm_slots = e.done + b.B;
+    e.roles = b.roles ? 1 : 0;
+    e.n_attr = b.n_attr;
+    e.n_sym = b.n_sym;
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);
     e.status = ctx->d_status;
     e.eps2 = eps2_of(ctx);
@@ -1299,9 +1335,26 @@ SPARKLING_API int sparkling_step(sparkling_ctx *ctx, void *K, int K_dtype, int64
     if (!is_device_ptr(K) || !is_device_ptr(grid->rho))
         return fail(ctx, SPARKLING_E_INVAL, "K and grid->rho must be device memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t N = Nc * Ns;
+    // The persistent engine takes the whole step in one launch (B = 1) where
+    // it applies: direct sums, a per-target fold it has, fixed iterations.
+    const bool engine_applies = ctx->attr_mode == SPARKLING_ATTRACTION_DIRECT &&
+                                ctx->rep_mode == SPARKLING_REPULSION_DIRECT &&
+                                (acc == SPARKLING_ACC_KAHAN32 || acc == SPARKLING_ACC_FP64) &&
+                                !(proj->tol > 0) && N >= 2 && N <= ((int64_t)1 << 31) - kTile;
+    if (engine_applies && (ctx->step_path == SPARKLING_STEP_ENGINE ||
+                           (ctx->step_path == SPARKLING_STEP_AUTO && N >= kStepEngineMin))) {
+        StepScope whole(ctx, st);
+        const int64_t off[2] = {0, N};
+        if ((s = sparkling_step_batched(ctx, 1, off, K, K_dtype, (int32_t)Ns, grid, &eta, proj, acc,
+                                        SPARKLING_BATCH_GRAPH, stream)))
+            return s;
+        whole.done();
+        return SPARKLING_OK;
+    }
     PairPlan P;
     Carve cv;
-    if ((s = plan_pairs(ctx, Nc * Ns, grid, acc, false, true, P, cv))) return s;
+    if ((s = plan_pairs(ctx, N, grid, acc, false, true, P, cv))) return s;
     ProjPlan L;
     if ((s = plan_project(ctx, K_dtype, Nc, Ns, cv, L))) return s;
     if ((s = ensure_ws(ctx, cv.off))) return s;
@@ -1551,6 +1604,8 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         b.one_launch = one_launch;
         b.sym = ctx->rep_symmetric && !one_launch;
         build_work_list(b, off, grids, ctas, ctx->items_per_cta, b.sym, b.one_launch);
+        b.roles = one_launch;
+        if (b.roles) split_work_list(b);
         Carve cv;
         b.o_pos = cv.take((size_t)off[B] * sizeof(float4));
         for (int t = 0; t < B; ++t) {
@@ -1559,7 +1614,7 @@ SPARKLING_API int sparkling_step_batched(sparkling_ctx *ctx, int32_t B, const in
         }
         b.o_traj = cv.take((size_t)B * sizeof(EngineTraj));
         b.o_items = cv.take(b.items.size() * sizeof(EngineItem));
-        b.o_cnt = cv.take((size_t)(B + 1) * sizeof(unsigned int));
+        b.o_cnt = cv.take((size_t)(3 + B + kSmSlots) * sizeof(unsigned int));
         int64_t parts = 0;
         for (int t = 0; t < B; ++t) parts += (int64_t)b.traj[t].tiles * b.traj[t].slots;
         b.o_part = cv.take((size_t)parts * kTile * sizeof(dacc4));
@@ -1800,6 +1855,15 @@ SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode)
     if (mode != SPARKLING_PROJECTION_FP64 && mode != SPARKLING_PROJECTION_MIXED)
         return fail(ctx, SPARKLING_E_INVAL, "projection mode %d is not FP64/MIXED", mode);
     ctx->proj_mode = mode;
+    return SPARKLING_OK;
+}
+
+SPARKLING_API int sparkling_set_step_path(sparkling_ctx *ctx, int path)
+{
+    if (!ctx) return fail(nullptr, SPARKLING_E_INVAL, "ctx is NULL");
+    if (path != SPARKLING_STEP_AUTO && path != SPARKLING_STEP_KERNELS && path != SPARKLING_STEP_ENGINE)
+        return fail(ctx, SPARKLING_E_INVAL, "step path %d is not AUTO/KERNELS/ENGINE", path);
+    ctx->step_path = path;
     return SPARKLING_OK;
 }
 

@@ -11,7 +11,11 @@
 // otherwise by the batched symmetric kernel before the launch; contexts
 // where that kernel cannot be resident get directed repulsion items (a run
 // of source blocks) interleaved with the attraction items instead.  Every
-// CTA of a single wave pulls the next item from a global counter.
+// CTA of a single wave pulls the next item from a global counter -- in the
+// one-launch shape from the counter of its role's part of the list (one CTA
+// in three per SM takes symmetric items first, the others attraction items
+// first: see next_item), so each SM runs SFU-bound and FP32-bound items side
+// by side.
 //
 // A pair item writes the FP64 partial sums of its tile into its own slot and
 // then bumps its trajectory's completion counter.  A projection item waits
@@ -21,9 +25,10 @@
 // item owns its slot and the slots are added in a fixed order, results do
 // not depend on which CTA ran which item.
 //
-// All items are dispensed in list order and all pair items precede all
-// projection items, so when a CTA waits on a trajectory every item it waits
-// for is already running on another CTA: the wait always ends.
+// Items are dispensed in list order (role dispatch: part by part) and a
+// projection item is dispensed only after all pair items of its trajectory,
+// so when a CTA waits on a trajectory every item it waits for is already
+// running on another CTA: the wait always ends.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -258,6 +263,36 @@ __device__ bool sym_item_run(const EngineArgs &e, const EngineTraj &tr, int64_t 
     return true;
 }
 
+// Index of the next item for this CTA (thread 0), n_items when none is left.
+// Role dispatch: the next projection item if its trajectory's pair items
+// are all done (claimed only then, so it never waits), else the CTA's own
+// pair part, then the other pair part, then any projection item -- taken
+// only once every pair item has been dispensed to a running CTA, so its
+// wait ends.
+template <bool SYM>
+__device__ __forceinline__ int next_item(const EngineArgs &e, int role)
+{
+    if (!SYM || !e.roles) return (int)atomicAdd(e.queue, 1u);
+    const int base_p = e.n_attr + e.n_sym;
+    const unsigned int n_p = (unsigned int)(e.n_items - base_p);
+    const unsigned int p = *(volatile unsigned int *)(e.queue + 2);
+    if (p < n_p) {
+        const int t = e.items[base_p + p].traj;
+        if (ld_acquire(e.done + t) >= (unsigned int)e.traj[t].n_pair_items &&
+            atomicCAS(e.queue + 2, p, p + 1) == p)
+            return base_p + (int)p;
+    }
+    for (int k = 0; k < 2; ++k) {
+        const int q = k == 0 ? role : 1 - role;
+        const unsigned int n = (unsigned int)(q == 0 ? e.n_attr : e.n_sym);
+        if (*(volatile unsigned int *)(e.queue + q) >= n) continue;
+        const unsigned int i = atomicAdd(e.queue + q, 1u);
+        if (i < n) return (q == 0 ? 0 : e.n_attr) + (int)i;
+    }
+    const unsigned int i = atomicAdd(e.queue + 2, 1u);
+    return i < n_p ? base_p + (int)i : e.n_items;
+}
+
 // REP: the work list may hold directed repulsion items (only when the
 // batched symmetric kernel cannot run); without them the kernel carries no
 // repulsion code.  SYM: the one-launch shape, whose work list holds the
@@ -278,9 +313,19 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) engine_kernel(const Eng
     }
     __syncthreads();
     uint32_t consumed = 0;
+    int role = 0;   // role dispatch: 0 attraction items first, 1 symmetric items first
+    if (SYM && e.roles) {
+        if (threadIdx.x == 0) {
+            unsigned int smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            bcast[2] = atomicAdd(e.sm_slots + (smid & (kSmSlots - 1)), 1u) % 3u == 2u ? 1 : 0;
+        }
+        __syncthreads();
+        role = bcast[2];
+    }
     for (;;) {
         if (threadIdx.x == 0)
-            bcast[0] = (int)atomicAdd(e.queue, 1u);
+            bcast[0] = next_item<SYM>(e, role);
         __syncthreads();
         const int idx = bcast[0];
         __syncthreads();

@@ -284,6 +284,7 @@ struct EngineTraj {
 };
 
 constexpr int kItemAttraction = 0, kItemRepulsion = 1, kItemProject = 2, kItemSym = 3;
+constexpr int kSmSlots = 512;         // per-SM counters of the role dispatch (%smid & 511)
 
 struct EngineItem {
     int32_t kind, traj;
@@ -300,8 +301,17 @@ struct EngineArgs {
     const float4 *pos;       // packed samples of all trajectories
     void *K;                 // [sum N][3], updated in place by the projection items
     dacc4 *part;
-    unsigned int *queue;     // next item (reset to 0 before every launch)
+    unsigned int *queue;     // next item: [3] (see roles) (reset to 0 before every launch)
     unsigned int *done;      // [B] completed pair items per trajectory (reset to 0)
+    // Role dispatch (one-launch shape): the list is attraction items
+    // [0, n_attr), symmetric items [n_attr, n_attr + n_sym), then projection
+    // items; queue[k] counts part k's dispensed items.  On every SM one CTA
+    // in three takes symmetric items first and the others attraction items
+    // first (sm_slots[kSmSlots] counts the CTAs that started on each SM);
+    // projection items are taken once both pair parts are dispensed.
+    int32_t roles = 0;
+    int32_t n_attr = 0, n_sym = 0;
+    unsigned int *sm_slots = nullptr;
     double *gstate;          // per-CTA projection state when it is not in shared memory
     unsigned long long *racc = nullptr;   // symmetric repulsion sums [sum N][3], or null
     float eps2 = kEps2;      // eps^2 (>= kEps2) added to every r^2

@@ -171,6 +171,11 @@ def test_argument_validation_before_any_cuda_call(lib):
         assert L.sparkling_set_shape(h, k, v) == lib.OK
     # projection arithmetic, wait budget, memory cap (host-side settings)
     assert L.sparkling_set_projection(h, 2) == lib.E_INVAL
+    assert L.sparkling_set_step_path(None, 0) == lib.E_INVAL
+    assert L.sparkling_set_step_path(h, 3) == lib.E_INVAL
+    assert L.sparkling_set_step_path(h, -1) == lib.E_INVAL
+    for v in (lib.STEP_ENGINE, lib.STEP_KERNELS, lib.STEP_AUTO):
+        assert L.sparkling_set_step_path(h, v) == lib.OK
     assert L.sparkling_set_projection(None, 0) == lib.E_INVAL
     for m in (lib.PROJECTION_MIXED, lib.PROJECTION_FP64):
         assert L.sparkling_set_projection(h, m) == lib.OK

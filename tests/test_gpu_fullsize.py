@@ -127,6 +127,32 @@ def test_diff_autograd_backward_and_finite_differences(sp, ctx):
     assert_grad_close(dK[idx, comp] * N, rich, "backward vs central differences")
 
 
+def test_hr_step_through_the_engine(sp, hr_oracle):
+    """The 1e7-sample step as the library runs it by default (one launch of
+    the persistent engine): with alpha = beta = inf and a loose box the
+    projection is the identity, so K' = K - G (eta = 1, K in FP64) exposes the
+    engine's gradient, checked against the oracle on the 8192 sampled
+    targets."""
+    p, idx, A0, R0, G0 = hr_oracle
+    c = sp.sparkling_create(0)
+    try:
+        sp.sparkling_set_timing(c, True)
+        K = torch.from_numpy(p.K.astype(np.float64)).cuda()
+        rho = torch.from_numpy(p.grid.rho).cuda()
+        g = sp.make_grid(rho, p.grid.lo, p.grid.hi, p.grid.n)
+        proj = sp.make_proj(float("inf"), float("inf"), 10.0, 2)
+        sp.sparkling_step(c, K, p.Nc, p.Ns, g, 1.0, proj)
+        sp.sparkling_status(c)
+        t = sp.sparkling_kernel_times(c)
+        out = K.cpu().numpy()
+    finally:
+        c.close()
+    assert t["engine"][1] == 1 and t["attraction"][1] == 0, t
+    G = p.K.astype(np.float64)[idx] - out[idx]
+    e, _ = assert_grad_close(G, G0, "engine G (HR step, 8192 targets)")
+    print(f"HR step through the engine: G rel L2 {e:.2e} on 8192 targets")
+
+
 def test_hr_sampled_targets_and_shots(sp, ctx, hr_oracle):
     """4096 x 2560 samples, 256^3 density (2.8e14 pairs): the gradient in the
     benchmark's launch configuration on 8192 random targets (G and R), zero

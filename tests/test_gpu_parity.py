@@ -274,15 +274,27 @@ def test_project_idempotent_on_feasible(sp, ctx):
     np.testing.assert_array_equal(Kd.cpu().numpy(), K)
 
 
-def test_step_tiny(sp, ctx):
+@pytest.mark.parametrize("path", ["kernels", "engine"])
+def test_step_tiny(sp, path):
+    """The projected-gradient step through either device path of
+    sparkling_step: the kernels in turn, or the one-launch persistent engine
+    (which the library takes for large steps)."""
     p = inputs.make_problem("tiny")
     pr = proj_of(p.proj, sp)
     ref = oracle.step(p.K, p.Nc, p.Ns, p.grid, p.eta, pr.alpha, pr.beta, pr.box, pr.pin_index,
                       tuple(pr.pin), pr.n_iter)
-    Kd = dev(p.K)
-    g = sp.make_grid(dev(p.grid.rho), p.grid.lo, p.grid.hi, p.grid.n)
-    sp.sparkling_step(ctx, Kd, p.Nc, p.Ns, g, p.eta, pr)
-    sp.sparkling_status(ctx)
+    c = sp.sparkling_create(0)
+    try:
+        sp.sparkling_set_step_path(c, path)
+        sp.sparkling_set_timing(c, True)
+        Kd = dev(p.K)
+        g = sp.make_grid(dev(p.grid.rho), p.grid.lo, p.grid.hi, p.grid.n)
+        sp.sparkling_step(c, Kd, p.Nc, p.Ns, g, p.eta, pr)
+        sp.sparkling_status(c)
+        t = sp.sparkling_kernel_times(c)
+    finally:
+        c.close()
+    assert (t["engine"][1] > 0) == (path == "engine") and t["step"][1] == 1
     np.testing.assert_allclose(Kd.cpu().numpy(), ref, rtol=0, atol=1e-8)
 
 
