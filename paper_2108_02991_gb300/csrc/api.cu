@@ -225,8 +225,12 @@ int check_limit(sparkling_ctx *ctx, size_t other, size_t bytes, const char *what
     return SPARKLING_OK;
 }
 
+// Every call carves the workspace from its start, so a call overwrites what
+// the batched step keeps there across calls (its uploaded work list and
+// descriptors): the batch is planned and uploaded again at its next call.
 int ensure_ws(sparkling_ctx *ctx, size_t bytes)
 {
+    ctx->batch.valid = false;
     if (bytes <= ctx->ws_bytes) return SPARKLING_OK;
     const size_t other = held_bytes(ctx) - ctx->ws_bytes;
     int s;

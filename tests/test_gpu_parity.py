@@ -298,6 +298,35 @@ def test_step_tiny(sp, path):
     np.testing.assert_allclose(Kd.cpu().numpy(), ref, rtol=0, atol=1e-8)
 
 
+def test_engine_step_after_a_gradient_call(sp):
+    """The engine keeps its planned work list in the context's workspace
+    across steps; a gradient call in between carves the same workspace, so
+    the next step must plan and upload its list again: the two steps agree
+    bit for bit and with the oracle."""
+    p = inputs.make_problem("tiny")
+    pr = proj_of(p.proj, sp)
+    ref = oracle.step(p.K, p.Nc, p.Ns, p.grid, p.eta, pr.alpha, pr.beta, pr.box, pr.pin_index,
+                      tuple(pr.pin), pr.n_iter)
+    c = sp.sparkling_create(0)
+    try:
+        sp.sparkling_set_step_path(c, "engine")
+        g = sp.make_grid(dev(p.grid.rho), p.grid.lo, p.grid.hi, p.grid.n)
+        outs = []
+        for _ in range(2):
+            Kd = dev(p.K)
+            sp.sparkling_step(c, Kd, p.Nc, p.Ns, g, p.eta, pr)
+            sp.sparkling_status(c)
+            outs.append(Kd.cpu().numpy())
+            # a larger gradient call overwrites the start of the workspace
+            Kb = dev(np.random.default_rng(5).uniform(-0.4, 0.4, size=(20000, 3)))
+            sp.sparkling_grad(c, Kb, g)
+            sp.sparkling_status(c)
+    finally:
+        c.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_allclose(outs[1], ref, rtol=0, atol=1e-8)
+
+
 def test_invalid_pointers_rejected(sp, ctx):
     """Host memory passed as a device pointer is refused before any launch."""
     K = torch.zeros(16, 3, dtype=torch.float64)
