@@ -30,6 +30,29 @@ def test_defaults_and_pair_count():
     assert bench.pairs_per_step(10, 7) == 10 * 7 + 10 * 9
 
 
+def test_constraint_excess_of_the_pattern():
+    """The bench line's constraint report: a straight constant-speed shot at
+    exactly the amplitude bound has excess 0 in alpha and -1 in beta (no
+    second differences), and doubling its speed makes the alpha excess 1;
+    samples beyond the box show as a positive box excess."""
+    import types
+    import numpy as np
+    import torch
+    import inputs
+    Ns, a, b, box = 8, 0.01, 0.001, 0.5
+    shot = np.zeros((Ns, 3))
+    shot[:, 0] = np.arange(Ns) * a - 0.03
+    probs = [types.SimpleNamespace(N=Ns, Nc=1, Ns=Ns, proj=inputs.Proj(a, b, box))]
+    w = types.SimpleNamespace(probs=probs, off=[0, Ns], host_current=True,
+                              Kh=torch.from_numpy(shot), K=None)
+    r = bench.Workload.constraint_excess(w)
+    assert abs(r["alpha_rel"]) < 1e-12 and r["beta_rel"] == pytest.approx(-1.0)
+    assert r["box"] == pytest.approx(max(abs(shot.min()), shot.max()) - box)
+    w.Kh = torch.from_numpy(2.0 * shot + np.array([0.0, 0.0, 0.6]))
+    r = bench.Workload.constraint_excess(w)
+    assert r["alpha_rel"] == pytest.approx(1.0) and r["box"] == pytest.approx(0.1)
+
+
 def _rank_main(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
                       WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
