@@ -413,9 +413,10 @@ SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode);
  * another value. */
 SPARKLING_API int sparkling_set_step_path(sparkling_ctx *ctx, int path);
 
-/* Budget of the context's bounded device waits (a TMA copy's mbarrier, the
- * batched step's wait for a trajectory's pair items), in SM clock cycles;
- * cycles < 0 restores the default 4e9 (about 2 s).  A wait that runs past it
+/* Budget of the context's bounded device waits (a TMA copy's mbarrier, and,
+ * with four times the budget, the persistent engine's wait for a
+ * trajectory's pair items, which other CTAs may have only just started), in
+ * SM clock cycles; cycles < 0 restores the default 4e9 (about 2 s).  A wait that runs past it
  * sets the status bit that makes the call (or the next sparkling_status)
  * return SPARKLING_E_TIMEOUT, and its kernel returns early, leaving its
  * outputs incomplete; the context stays usable.  After a timeout a CTA still

@@ -63,13 +63,16 @@ __device__ __forceinline__ void mark_done(unsigned int *done)
 }
 
 // Bounded wait until *done >= target; false (and the timeout status bit) if
-// it does not happen within the context's wait budget.
+// it does not happen within four times the context's wait budget: the items
+// waited for may have started just before, and the largest (an attraction
+// item over a whole 256^3 density) takes ~3.5e9 cycles of one CTA, close to
+// the default budget of a copy wait.
 __device__ bool wait_done(const unsigned int *done, unsigned int target, int *status, int *flag)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire(done) < target) {
-            const long long budget = wait_budget(status);
+            const long long budget = 4 * wait_budget(status);
             const long long t0 = clock64();
             while (ld_acquire(done) < target) {
                 if (clock64() - t0 > budget) {
