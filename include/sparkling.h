@@ -414,7 +414,8 @@ SPARKLING_API int sparkling_set_projection(sparkling_ctx *ctx, int mode);
 SPARKLING_API int sparkling_set_step_path(sparkling_ctx *ctx, int path);
 
 /* Budget of the context's bounded device waits (a TMA copy's mbarrier, and,
- * with four times the budget, the persistent engine's wait for a
+ * with a multiple of the budget -- four, or more where one pair item of the
+ * work list may take longer -- the persistent engine's wait for a
  * trajectory's pair items, which other CTAs may have only just started), in
  * SM clock cycles; cycles < 0 restores the default 4e9 (about 2 s).  A wait that runs past it
  * sets the status bit that makes the call (or the next sparkling_status)

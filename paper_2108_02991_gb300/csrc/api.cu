@@ -84,6 +84,7 @@ struct sparkling_ctx {
         bool one_launch = false;          // symmetric repulsion items in the engine's work list
         bool roles = false;               // role dispatch over the list's three parts
         int32_t n_attr = 0, n_sym = 0;    // sizes of its attraction and symmetric parts
+        int32_t wait_scale = 4;           // projection waits: this many wait budgets
         size_t o_racc = 0, o_symtraj = 0;
         int64_t sym_units = 0;
         std::vector<SymTraj> symtraj;
@@ -1011,6 +1012,14 @@ void build_work_list(sparkling_ctx::Batch &b, const std::vector<int64_t> &off,
             project_items(released++);
     }
     while (released < B) project_items(released++);
+    // A projection item may wait for a pair item that another CTA has only
+    // just started: allow twice the longest item's time at a conservative 4
+    // pairs per CTA per clock (measured: ~4.8 for attraction, ~5.3 directed
+    // repulsion pairs), and never less than four wait budgets.
+    double most = 0.0;
+    for (double v : b.item_pairs) most = std::max(most, v);
+    const double scale = std::ceil(2.0 * most / 4.0 / (double)kWaitCycles);
+    b.wait_scale = (int32_t)std::min(1024.0, std::max(4.0, scale));
 }
 
 // Role dispatch: the list reordered into its attraction items, its
@@ -1103,6 +1112,7 @@ int batch_engine(sparkling_ctx *ctx, void *K, int K_dtype, int acc, int variant,
     e.done = e.queue + 3;
     e.sm_slots = e.done + b.B;
     e.roles = b.roles ? 1 : 0;
+    e.wait_scale = b.wait_scale;
     e.n_attr = b.n_attr;
     e.n_sym = b.n_sym;
     e.gstate = b.proj_in_smem ? nullptr : at<double>(ctx, b.o_gstate);

@@ -63,16 +63,18 @@ __device__ __forceinline__ void mark_done(unsigned int *done)
 }
 
 // Bounded wait until *done >= target; false (and the timeout status bit) if
-// it does not happen within four times the context's wait budget: the items
-// waited for may have started just before, and the largest (an attraction
-// item over a whole 256^3 density) takes ~3.5e9 cycles of one CTA, close to
-// the default budget of a copy wait.
-__device__ bool wait_done(const unsigned int *done, unsigned int target, int *status, int *flag)
+// it does not happen within `scale` times the context's wait budget: the
+// items waited for may have started just before, and one item can take a
+// large part of a copy wait's budget (an attraction item over a whole 256^3
+// density: ~3.5e9 cycles of one CTA), so the host sizes the scale from the
+// work list's largest item.
+__device__ bool wait_done(const unsigned int *done, unsigned int target, int scale, int *status,
+                          int *flag)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire(done) < target) {
-            const long long budget = 4 * wait_budget(status);
+            const long long budget = scale * wait_budget(status);
             const long long t0 = clock64();
             while (ld_acquire(done) < target) {
                 if (clock64() - t0 > budget) {
@@ -134,7 +136,8 @@ template <typename KT>
 __device__ __noinline__ bool project_item(const EngineArgs &e, const EngineItem &item,
                                           const EngineTraj &tr, unsigned char *region, int *bcast)
 {
-    if (!wait_done(e.done + item.traj, (unsigned int)tr.n_pair_items, e.status, bcast + 1))
+    if (!wait_done(e.done + item.traj, (unsigned int)tr.n_pair_items, e.wait_scale, e.status,
+                   bcast + 1))
         return false;
     const int Ns = tr.Ns;
     double *base = e.proj_in_smem ? reinterpret_cast<double *>(region)

@@ -312,6 +312,10 @@ struct EngineArgs {
     int32_t roles = 0;
     int32_t n_attr = 0, n_sym = 0;
     unsigned int *sm_slots = nullptr;
+    // A projection item waits for its trajectory's pair items up to
+    // wait_scale times the context's wait budget (at least 4; more where the
+    // largest pair item may take longer, see api.cu).
+    int32_t wait_scale = 4;
     double *gstate;          // per-CTA projection state when it is not in shared memory
     unsigned long long *racc = nullptr;   // symmetric repulsion sums [sum N][3], or null
     float eps2 = kEps2;      // eps^2 (>= kEps2) added to every r^2
